@@ -1,0 +1,232 @@
+/*
+ * mst.h — C ABI of libmst: minimum spanning trees by data-parallel Boruvka
+ * rounds on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (Boruvka; "Parallel Minimum Spanning Tree Algorithms and
+ * Evaluation", Section 2.1) repeats rounds until no edge joins two
+ * components: every component picks its lightest outgoing edge, those edges
+ * are added to the tree M and the components they join are merged.  The
+ * paper's "Optimization" (Section 2.1) drops edges that have become internal
+ * to a component; here they are removed physically every round.
+ *
+ * Problem (Section 1 defines the tree, Section 2.1 "Inputs" the graph): an
+ * undirected graph with n vertices 0..n-1 and m edges given as COO arrays
+ * src[m], dst[m] and weights w[m]; edge id e is the index into these arrays.
+ * The result is the minimum spanning tree, or the minimum spanning forest
+ * when the graph is not connected.  The paper assumes distinct weights; this
+ * library accepts ties and breaks them by edge id (the lighter of two edges
+ * with equal weight is the one with the smaller id), which makes the result
+ * unique for every input.  Self-loops and parallel edges are allowed.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named src, dst, w, out_*, *_off are DEVICE pointers, owned by
+ *     the caller, and must stay valid until the work queued on `stream`
+ *     completes.  `stream` is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream).  Calls are asynchronous: they return after
+ *     queueing work; results are ready when the stream reaches that point.
+ *   - Argument errors are detected on the host, before any work is queued,
+ *     and returned synchronously.  Conditions found on the device (a vertex
+ *     id out of range, a NaN weight, a disconnected graph, a bounded wait
+ *     that ran out) are recorded in a device status word that
+ *     mst_get_status() returns; an out-of-range edge is ignored and a NaN
+ *     weight sorts after every other weight.
+ *   - A handle owns device workspace sized for the largest problem it has
+ *     solved; it grows on demand (cudaMalloc) and is freed by mst_destroy.
+ *     A handle is not thread-safe and its workspace is shared by all calls
+ *     on it: use one handle per host thread and per stream.
+ *   - Limits: 0 <= n <= 2^31-1, 0 <= m <= 2^31-1.
+ */
+#ifndef MST_H
+#define MST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mst_handle_s *mst_handle;
+
+typedef enum {
+    MST_OK = 0,
+    MST_ERR_INVALID_ARG = 1,  /* bad argument (host) or bad vertex id / NaN (device) */
+    MST_ERR_OOM = 2,          /* device allocation failed */
+    MST_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    MST_ERR_DISCONNECTED = 4, /* informational: the result is a spanning forest */
+    MST_ERR_TIMEOUT = 5,      /* a bounded device wait gave up; results invalid */
+    MST_ERR_BUDGET = 6,       /* the request does not fit the memory budget */
+    MST_ERR_INTERNAL = 7      /* an internal consistency check failed */
+} mst_status;
+
+typedef enum {
+    MST_W_U32 = 0, /* uint32 weights, compared as unsigned integers */
+    MST_W_F32 = 1  /* float32 weights, compared as floats; -0 equals +0 */
+} mst_weight_type;
+
+/* Human-readable name of a status code (static string). */
+const char *mst_status_string(mst_status s);
+
+/*
+ * Creates a handle on CUDA device `device`.  mem_budget_bytes caps the
+ * workspace this handle may allocate (0 = no cap); a solve whose workspace
+ * would exceed it returns MST_ERR_BUDGET.  *h receives the handle.
+ */
+mst_status mst_create(mst_handle *h, int device, size_t mem_budget_bytes);
+
+/* Waits for the handle's work, frees its workspace and the handle. */
+mst_status mst_destroy(mst_handle h);
+
+/*
+ * Minimum spanning tree of one graph with uint32 weights (Section 2.1 rounds).
+ *   n, m          vertex and edge counts.
+ *   src, dst      int32[m] edge endpoints in [0, n).
+ *   w             uint32[m] weights.
+ *   out_edge_ids  int32 capacity >= max(n-1, 0): receives the ids of the
+ *                 tree edges in ascending order.
+ *   out_count     one int64: receives the number of ids written
+ *                 (n - number of connected components).
+ * Runs asynchronously on `stream`.  Returns MST_ERR_INVALID_ARG for negative
+ * or too-large sizes, NULL pointers with nonzero sizes, or a NULL handle.
+ */
+mst_status mst_solve(mst_handle h, int32_t n, int64_t m,
+                     const int32_t *src, const int32_t *dst, const void *w,
+                     int32_t *out_edge_ids, int64_t *out_count, void *stream);
+
+/* As mst_solve, with the weight type given explicitly (uint32 or float32). */
+mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
+                        const int32_t *src, const int32_t *dst, const void *w,
+                        int32_t *out_edge_ids, int64_t *out_count, void *stream);
+
+/*
+ * Host-buffer form of mst_solve_ex for callers whose graph is in host memory:
+ * copies src, dst and w (host pointers; page-locked memory copies fastest)
+ * into device staging owned by the handle, solves, copies the tree's edge
+ * ids (host int32 capacity >= max(n-1,0)) and *out_count (host int64) back,
+ * and returns after the result is in host memory (synchronises `stream`).
+ * Returns an argument error, or else the device status as mst_get_status.
+ */
+mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
+                          const int32_t *src, const int32_t *dst, const void *w,
+                          int32_t *out_edge_ids, int64_t *out_count, void *stream);
+
+/*
+ * Minimum spanning trees of G independent graphs in one launch.
+ *   vtx_off, edge_off  int64[G+1] device offset tables: graph g has
+ *                      n_g = vtx_off[g+1]-vtx_off[g] vertices and edges
+ *                      edge_off[g] .. edge_off[g+1]-1 of src/dst/w.
+ *   src, dst           int32 endpoints, LOCAL to their graph (0..n_g-1).
+ *   w                  uint32 or float32 weights (per `wt`).
+ *   total_n, total_m   vtx_off[G] and edge_off[G] (used to size workspace;
+ *                      a mismatch found on the device is MST_ERR_INVALID_ARG).
+ *   out_edge_ids       int32[total_n]: graph g writes its tree's LOCAL edge
+ *                      ids, ascending, at out_edge_ids + vtx_off[g].
+ *   out_counts         int64[G]: number of ids written for each graph.
+ * Each graph's result is the same as mst_solve_ex on that graph alone.
+ * Constraints per graph: n_g, m_g <= 2^31-1.
+ */
+mst_status mst_solve_batched(mst_handle h, mst_weight_type wt, int32_t G,
+                             const int64_t *vtx_off, const int64_t *edge_off,
+                             int64_t total_n, int64_t total_m,
+                             const int32_t *src, const int32_t *dst, const void *w,
+                             int32_t *out_edge_ids, int64_t *out_counts, void *stream);
+
+/*
+ * Synchronises `stream` and returns the device status of the handle's last
+ * solve: MST_OK, MST_ERR_DISCONNECTED (forest written), MST_ERR_INVALID_ARG
+ * (bad vertex id or NaN weight seen), MST_ERR_TIMEOUT or MST_ERR_INTERNAL.
+ * The status word is cleared at the start of each solve.
+ */
+mst_status mst_get_status(mst_handle h, void *stream);
+
+/*
+ * Per-round sizes of the handle's last single-graph solve (synchronises
+ * `stream`): live_edges[r] = edges entering round r (round 0 = m),
+ * live_vertices[r] = components entering round r; *rounds = number of
+ * rounds run.  At most `cap` entries are written.  Used to count the bytes
+ * the method moves.
+ */
+mst_status mst_get_round_stats(mst_handle h, void *stream, int64_t *live_edges,
+                               int64_t *live_vertices, int32_t cap, int32_t *rounds);
+
+/* Time and traffic model of one kernel of a solve (see mst_profile_last_solve). */
+typedef struct {
+    char name[32];       /* kernel name, e.g. "k_compact<R>" */
+    int32_t launches;    /* launches in the solve */
+    double total_ms;     /* sum of CUDA-event durations of those launches */
+    double alg_bytes;    /* algorithmic DRAM bytes of those launches (model) */
+} mst_kernel_profile;
+
+/*
+ * Re-runs the handle's last single-graph solve (same device buffers, which
+ * must still be valid) launching each kernel separately between two CUDA
+ * events on `stream`, and reports per kernel the launch count, the summed
+ * event time and the bytes the method must move through DRAM in those
+ * launches (edge lists and per-vertex arrays; label gathers and atomics,
+ * which stay in L2, are not counted).  Writes at most `cap` entries and sets
+ * *count.  Synchronises `stream`; the outputs are written again.
+ */
+mst_status mst_profile_last_solve(mst_handle h, void *stream, mst_kernel_profile *out,
+                                  int32_t cap, int32_t *count);
+
+/*
+ * Schedule control for the batched solver (the autotuner's knob).
+ * schedule: 0 = automatic (cached autotune result per size bucket, else the
+ * built-in default), 1 = one thread block per graph, 2 = one warp per graph
+ * for small graphs and a block per graph otherwise.  block_threads: 128,
+ * 256, 512 or 1024 (0 = automatic).
+ */
+mst_status mst_set_batched_schedule(mst_handle h, int schedule, int block_threads);
+
+/*
+ * Autotunes the batched solver on the given batch (same arguments as
+ * mst_solve_batched): times each candidate schedule once per size bucket,
+ * keeps the fastest, and, when cache_path is not NULL, stores the choice as
+ * JSON there (and loads it on later calls).  Synchronises `stream`.
+ */
+mst_status mst_autotune_batched(mst_handle h, mst_weight_type wt, int32_t G,
+                                const int64_t *vtx_off, const int64_t *edge_off,
+                                int64_t total_n, int64_t total_m,
+                                const int32_t *src, const int32_t *dst, const void *w,
+                                int32_t *out_edge_ids, int64_t *out_counts,
+                                const char *cache_path, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * Continuous-batching server on top of the batched solver.  A host thread
+ * admits submitted graphs under the handle's memory budget, launches each
+ * admitted group as one batched solve on one of `streams` CUDA streams, and
+ * admits new requests as soon as a stream and memory are free, so solves of
+ * requests that arrive while others run overlap on the GPU.  max_batch caps
+ * the graphs per launch.
+ */
+mst_status mst_server_start(mst_handle h, int streams, int max_batch);
+
+/*
+ * Queues one graph (device pointers, as in mst_solve_ex; they must stay
+ * valid until the request completes).  *ticket receives the request id.
+ * The submit time is taken now; latency = completion - submit.
+ */
+mst_status mst_submit(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
+                      const int32_t *src, const int32_t *dst, const void *w,
+                      int32_t *out_edge_ids, int64_t *out_count, uint64_t *ticket);
+
+/*
+ * Non-blocking poll: *done = 1 once the request's outputs are written.
+ * When done and latency_us is not NULL, *latency_us = completion - submit in
+ * microseconds (host clock, completion seen by the server thread).
+ */
+mst_status mst_poll(mst_handle h, uint64_t ticket, int *done, double *latency_us);
+
+/* Blocks until every submitted request has completed. */
+mst_status mst_server_drain(mst_handle h);
+
+/* Drains, stops the server thread and releases its streams. */
+mst_status mst_server_stop(mst_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MST_H */

@@ -1,0 +1,319 @@
+// mst_common.cuh — device-side building blocks shared by the single-graph
+// and batched Boruvka solvers: the control block, the workspace layout, the
+// edge key, ballot-based tile ranking and the decoupled look-back scan.
+//
+// Edge key (Section 2.1, steps 21 and 24 compare weights; ties are broken by
+// edge position): key = (weight_bits << 32) | position.  weight_bits is the
+// uint32 weight, or for float32 an order-preserving remap of the IEEE bits.
+// position is the edge's index in the live edge list of the current round;
+// every compaction is stable, so position order equals input edge-id order
+// among the edges that are still alive, and min over keys is min over
+// (weight, edge id).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mst {
+
+constexpr int kThreads = 256;                 // threads per block, streaming kernels
+constexpr int kWarps = kThreads / 32;         // 8
+constexpr int kItems = 4;                     // items per thread per tile
+constexpr int kTile = kThreads * kItems;      // 1024 items per tile
+static_assert(kItems * kWarps == 32, "tile ranking scans 32 (row, warp) counts in one warp");
+constexpr int kMaxRounds = 64;                // > log2(2^31) + 1: never reached
+constexpr uint64_t kNoEdge = ~0ull;           // minimum[] = -1 of Section 2.1
+constexpr int kChaseLimit = 64;               // pointer hops per thread per pass
+constexpr uint32_t kMaxJumpPasses = 64;       // > log2(2^31): pointer jumping ends sooner
+constexpr uint32_t kSpinLimit = 1u << 22;     // iterations of any device wait
+
+// Device status bits (mapped to mst_status on the host).
+enum : uint32_t {
+    ST_BAD_VERTEX = 1u,
+    ST_NAN = 2u,
+    ST_TIMEOUT = 4u,
+    ST_INTERNAL = 8u,
+    ST_DISCONNECTED = 16u,
+    ST_BAD_OFFSETS = 32u,
+};
+
+// Control block of one single-graph solve, in device memory.  Kernels of a
+// captured round read it at block start; only the last block of a kernel
+// (see last_block_done) advances it, after every other block has finished.
+struct Ctl {
+    const int32_t *src;
+    const int32_t *dst;
+    const void *w;
+    int32_t *out;
+    int64_t *out_count;
+    uint32_t n, m, wt, vec_ok;
+    uint32_t round;   // current round r
+    uint32_t n_cur;   // components entering round r (ids 0..n_cur-1)
+    uint32_t m_cur;   // live edges entering round r
+    uint32_t n_next;  // components after round r (written by hook)
+    uint32_t m_next;  // live edges after round r (written by compaction)
+    uint32_t epoch;   // look-back descriptor epoch, +1 per scanning kernel
+    uint32_t ticket;  // tile ticket of the running kernel
+    uint32_t done;    // finished-block counter of the running kernel
+    uint32_t deep;    // some pointer chase did not reach its root
+    uint32_t deep_seen;  // value of deep at the end of the last compress pass
+    uint32_t passes;     // follow-up compress passes in the current round
+    uint32_t status;  // ST_* bits
+    uint32_t stat_m[kMaxRounds + 1];
+    uint32_t stat_n[kMaxRounds + 1];
+};
+
+// Workspace of the single-graph solver.  E[] holds live edge records
+// (u, v, weight_bits, input edge id); mins[] the per-component minimum key,
+// double-buffered by round parity.
+struct Ws {
+    Ctl *ctl;
+    uint4 *E[2];
+    unsigned long long *mins[2];
+    int32_t *parent;   // hook pointer of each component (itself for a root)
+    int32_t *nid;      // new dense id of each root
+    int32_t *lab;      // new id of each component after compression
+    uint32_t *mst_bits;
+    unsigned long long *desc;  // look-back descriptors
+    uint32_t n_cap, m_cap, desc_cap;
+};
+
+// ---------------------------------------------------------------- weights
+
+__device__ __forceinline__ uint32_t weight_bits_f32(uint32_t b, uint32_t *status)
+{
+    if ((b & 0x7fffffffu) > 0x7f800000u) {  // NaN
+        atomicOr(status, ST_NAN);
+        return 0xffffffffu;
+    }
+    if (b == 0x80000000u)
+        b = 0;  // -0 -> +0
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ uint32_t weight_bits(uint32_t raw, uint32_t wt, uint32_t *status)
+{
+    return wt ? weight_bits_f32(raw, status) : raw;
+}
+
+__device__ __forceinline__ unsigned long long make_key(uint32_t wbits, uint32_t pos)
+{
+    return ((unsigned long long)wbits << 32) | pos;
+}
+
+// ------------------------------------------------------------ memory helpers
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p)
+{
+    return *(const volatile uint32_t *)p;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------ tile ranking
+
+// Striped tile layout: item j of thread t is tile index j*kThreads + t, so
+// every load instruction of a warp is contiguous.  Given keep flags, returns
+// each kept item's rank among the tile's kept items in index order (stable)
+// and the tile's total.  s32 is 33 words of shared memory.
+__device__ __forceinline__ void tile_ranks_striped(const bool (&keep)[kItems],
+                                                   uint32_t (&rank)[kItems],
+                                                   uint32_t &total, uint32_t *s32)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t mask[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; j++)
+        mask[j] = __ballot_sync(0xffffffffu, keep[j]);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < kItems; j++)
+            s32[j * kWarps + warp] = __popc(mask[j]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = s32[lane], incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        s32[lane] = incl - v;
+        if (lane == 31)
+            s32[32] = incl;
+    }
+    __syncthreads();
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kItems; j++)
+        rank[j] = s32[j * kWarps + warp] + __popc(mask[j] & lt);
+    total = s32[32];
+}
+
+// Blocked tile layout: items j of thread t are tile indices 4t .. 4t+3 (one
+// 128-bit load per array).  Same contract as tile_ranks_striped.
+__device__ __forceinline__ void tile_ranks_blocked(const bool (&keep)[kItems],
+                                                   uint32_t (&rank)[kItems],
+                                                   uint32_t &total, uint32_t *s32)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    uint32_t before = 0, wcount = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+        uint32_t mk = __ballot_sync(0xffffffffu, keep[j]);
+        before += __popc(mk & lt);
+        wcount += __popc(mk);
+    }
+    if (lane == 0)
+        s32[warp] = wcount;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < kWarps ? s32[lane] : 0, incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane < kWarps)
+            s32[lane] = incl - v;
+        if (lane == 31)
+            s32[32] = incl;
+    }
+    __syncthreads();
+    uint32_t run = s32[warp] + before;
+#pragma unroll
+    for (int j = 0; j < kItems; j++) {
+        rank[j] = run;
+        run += keep[j] ? 1u : 0u;
+    }
+    total = s32[32];
+}
+
+// ------------------------------------------------- decoupled look-back scan
+//
+// Single-pass prefix sum over tiles (Merrill & Garland, "Single-pass Parallel
+// Prefix Scan with Decoupled Look-back", 2016).  Tiles are taken in order
+// from an atomic ticket, so every predecessor of a waiting tile has already
+// started and the wait ends.  A descriptor is one 64-bit word:
+//   bits 0..30 value, bits 31..32 flag (1 aggregate, 2 inclusive prefix),
+//   bits 33..63 epoch (a descriptor from another epoch reads as empty).
+// Every wait is bounded by kSpinLimit; on expiry ST_TIMEOUT is set and the
+// scan continues with a wrong value rather than hanging.
+
+constexpr unsigned long long kDescAgg = 1ull << 31;
+constexpr unsigned long long kDescPrefix = 2ull << 31;
+
+__device__ __forceinline__ unsigned long long desc_word(uint32_t epoch, unsigned long long flag,
+                                                        uint32_t value)
+{
+    return ((unsigned long long)(epoch & 0x7fffffffu) << 33) | flag | (value & 0x7fffffffu);
+}
+
+// Called by all 32 lanes of warp 0.  Publishes the tile's aggregate, looks
+// back over predecessors 32 at a time, publishes the inclusive prefix and
+// returns the exclusive prefix (same value in every lane).
+__device__ __forceinline__ uint32_t lookback_warp(unsigned long long *desc, uint32_t tile,
+                                                  uint32_t aggregate, uint32_t epoch,
+                                                  uint32_t *status)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long ep = (unsigned long long)(epoch & 0x7fffffffu);
+    if (tile == 0) {
+        if (lane == 0)
+            st_relaxed_u64(&desc[0], desc_word(epoch, kDescPrefix, aggregate));
+        return 0;
+    }
+    if (lane == 0)
+        st_relaxed_u64(&desc[tile], desc_word(epoch, kDescAgg, aggregate));
+    uint32_t excl = 0;
+    int64_t hi = (int64_t)tile - 1;  // nearest predecessor not yet summed
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t idx = hi - lane;
+        unsigned long long d;
+        uint32_t flag, val;
+        if (idx >= 0) {
+            d = ld_relaxed_u64(&desc[idx]);
+            flag = (d >> 33) == ep ? (uint32_t)((d >> 31) & 3u) : 0u;
+            val = (uint32_t)(d & 0x7fffffffu);
+        } else {
+            flag = 2u;  // before tile 0: prefix 0
+            val = 0u;
+        }
+        const uint32_t pmask = __ballot_sync(0xffffffffu, flag == 2u);
+        const uint32_t zmask = __ballot_sync(0xffffffffu, flag == 0u);
+        const uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 32u;
+        const uint32_t need = stop == 32u ? 0xffffffffu : ((2u << stop) - 1u);
+        if (zmask & need) {  // an unpublished tile before the nearest prefix: wait
+            if (++spins > kSpinLimit) {
+                if (lane == 0)
+                    atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(20);
+            continue;
+        }
+        uint32_t part = ((uint32_t)lane <= stop) ? val : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+        excl += part;
+        if (stop != 32u)
+            break;
+        hi -= 32;
+    }
+    if (lane == 0)
+        st_relaxed_u64(&desc[tile], desc_word(epoch, kDescPrefix, excl + aggregate));
+    return excl;
+}
+
+// ------------------------------------------------------- block coordination
+
+// Takes the next tile index from *ticket (thread 0) and broadcasts it.
+__device__ __forceinline__ uint32_t next_tile(uint32_t *ticket, uint32_t *s_tile)
+{
+    __syncthreads();  // everyone has read the previous value
+    if (threadIdx.x == 0)
+        *s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    return *s_tile;
+}
+
+// Returns true in exactly one block: the last one to reach this point.  All
+// writes of all other blocks are visible to it afterwards.
+__device__ __forceinline__ bool last_block_done(uint32_t *done, uint32_t *s_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(done, 1u);
+        *s_flag = (prev == gridDim.x - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    const bool last = *s_flag != 0u;
+    if (last)
+        __threadfence();
+    return last;
+}
+
+}  // namespace mst

@@ -1,0 +1,140 @@
+// mst_internal.h — host-side declarations shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/mst.h"
+#include "mst_common.cuh"
+
+namespace mst {
+
+// ------------------------------------------------------------ single graph
+
+// Workspace and captured round loop of the single-graph solver.
+struct Single {
+    Ws ws{};
+    void *base = nullptr;   // one cudaMalloc carved into the Ws arrays
+    size_t bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid_tiles = 0;     // persistent grid of the tile kernels
+    int grid_stream = 0;    // grid of the grid-stride kernels
+    uint64_t solves = 0;    // solves since the descriptors were last cleared
+};
+
+struct KernelProfile {
+    std::string name;
+    int launches;
+    double ms;
+    double bytes;
+};
+
+// Workspace bytes for capacities (n_cap, m_cap).
+size_t single_bytes(uint32_t n_cap, uint32_t m_cap);
+// Allocates (or grows) the workspace and rebuilds the graph.
+cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m);
+void single_release(Single &s);
+// Queues one solve on `stream` (arguments already validated).
+cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, const void *w,
+                          uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n,
+                          uint32_t m, cudaStream_t stream);
+// Replays a solve kernel by kernel between CUDA events (synchronous).
+cudaError_t single_profile(Single &s, const int32_t *src, const int32_t *dst, const void *w,
+                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n, uint32_t m,
+                           cudaStream_t stream, std::vector<KernelProfile> &prof);
+
+// ------------------------------------------------------------------ batched
+
+// Per-size-bucket schedule of the batched solver.
+struct BatchedConfig {
+    int schedule = 0;       // 1 block per graph, 2 warp per small graph
+    int block_threads = 0;  // 0 = automatic
+};
+
+struct Batched {
+    void *base = nullptr;
+    size_t bytes = 0;
+    uint64_t n_cap = 0, m_cap = 0;
+    int32_t g_cap = 0;
+    void *ctl = nullptr;    // batched control words (inside base)
+    int schedule = 0;       // forced schedule (0 = autotuned/default)
+    int block_threads = 0;  // forced block size (0 = autotuned/default)
+    std::map<int, BatchedConfig> tuned;  // size bucket -> choice
+    bool tuned_loaded = false;
+};
+
+size_t batched_bytes(int32_t G, uint64_t n, uint64_t m);
+cudaError_t batched_reserve(Batched &b, int32_t G, uint64_t n, uint64_t m);
+void batched_release(Batched &b);
+cudaError_t batched_launch(Batched &b, int device, uint32_t wt, int32_t G, const int64_t *vtx_off,
+                           const int64_t *edge_off, uint64_t total_n, uint64_t total_m,
+                           const int32_t *src, const int32_t *dst, const void *w, int32_t *out,
+                           int64_t *out_counts, cudaStream_t stream);
+uint32_t batched_status_bits(Batched &b, cudaStream_t stream, cudaError_t *err);
+
+// ------------------------------------------------------------------ serving
+
+struct Request {
+    uint64_t ticket;
+    uint32_t wt;
+    int32_t n;
+    int64_t m;
+    const int32_t *src, *dst;
+    const void *w;
+    int32_t *out;
+    int64_t *out_count;
+    double t_submit_us;
+    size_t footprint;
+};
+
+struct Server;
+
+// ------------------------------------------------------------------ handle
+
+enum LastKind { LAST_NONE = 0, LAST_SINGLE = 1, LAST_BATCHED = 2 };
+
+}  // namespace mst
+
+// Arguments of the last single-graph solve (for mst_profile_last_solve).
+struct LastSolve {
+    const int32_t *src = nullptr, *dst = nullptr;
+    const void *w = nullptr;
+    int32_t *out = nullptr;
+    int64_t *out_count = nullptr;
+    uint32_t n = 0, m = 0, wt = 0;
+    bool valid = false;
+};
+
+struct mst_handle_s {
+    int device = 0;
+    LastSolve last_solve;
+    void *staging = nullptr;  // device staging of mst_solve_host
+    size_t staging_bytes = 0;
+    size_t budget = 0;  // 0 = unlimited
+    int num_sms = 0;
+    mst::Single single;
+    mst::Batched batched;
+    mst::LastKind last = mst::LAST_NONE;
+    mst::Server *server = nullptr;
+};
+
+namespace mst {
+mst_status status_from_bits(uint32_t bits);
+double now_us();
+mst_status server_start(mst_handle h, int streams, int max_batch);
+mst_status server_submit(mst_handle h, const Request &r, uint64_t *ticket);
+mst_status server_poll(mst_handle h, uint64_t ticket, int *done, double *latency_us);
+mst_status server_drain(mst_handle h);
+mst_status server_stop(mst_handle h);
+}  // namespace mst

@@ -54,59 +54,77 @@ def peaks():
 
 
 class ClockSampler:
-    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+    """Samples SM clocks and throttle reasons with nvidia-smi (every 50 ms)
+    from before warm-up to after the timed region; summary() keeps the
+    samples taken inside the timed window (or, when the window is shorter
+    than the sampling period, the samples around it, and says so)."""
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.file = None
+        self.path = None
+        self.window = None
 
-    def __enter__(self):
+    def start(self):
         try:
-            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.file, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5
+            while time.time() < deadline and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
-    def __exit__(self, *a):
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
         if self.proc is not None:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+            self.fh.close()
 
     def summary(self):
-        if self.proc is None or self.file is None:
+        if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.file.flush()
+        import datetime
         rows = []
-        for line in open(self.file.name):
+        for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                rows.append(f)
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), [x.lower() == "active" for x in f[6:10]]))
             except ValueError:
-                pass
-        os.unlink(self.file.name)
+                continue
+        os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        t0, t1 = self.window or (rows[0][0], rows[-1][0])
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        where = "inside the timed region"
+        if not inside:  # region shorter than the sampling period
+            inside = sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:3]
+            where = "nearest to a timed region shorter than the 50 ms sampling period"
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[3][i]})
+        return {"sm_mhz": statistics.median(r[1] for r in inside),
+                "sm_max_mhz": max(r[2] for r in inside), "reasons": reasons,
+                "samples": len(inside), "where": where}
 
 
 def dist_env():
@@ -164,6 +182,33 @@ def run_reference(args):
     return 0
 
 
+def run_e2e(B, h, g, ws, stream, args):
+    """Same metric through mst_solve_host: pinned host inputs copied in and
+    the tree copied out inside every timed step."""
+    import torch
+    hs = torch.from_numpy(g.src).pin_memory()
+    hd = torch.from_numpy(g.dst).pin_memory()
+    hw = torch.from_numpy(g.w.view(np.int32)).pin_memory()
+    ho = torch.empty(max(g.n - 1, 1), dtype=torch.int32).pin_memory()
+    hc = torch.zeros(1, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        B.mst_solve_host(h, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc, stream)
+    steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = B.mst_solve_host(h, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc, stream)
+        if st != B.MST_OK:
+            raise B.MstError(st, "mst_solve_host")
+    dt = (time.perf_counter() - t0) / steps
+    if int(hc.item()) != g.n - 1:
+        raise RuntimeError("e2e self-check failed")
+    return {"value": ws * g.m / dt / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": 12 * g.m, "d2h_bytes_per_step": 4 * (g.n - 1) + 8,
+            "ms_per_step": dt * 1e3, "steps": steps,
+            "timer": "host wall clock around the blocking mst_solve_host call"}
+
+
 def run_ours(args):
     import torch
 
@@ -206,19 +251,24 @@ def run_ours(args):
                            f"count {int(cnt.item())} != {g.n - 1}")
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = ClockSampler(dev).start()
+    for _ in range(3):
+        solve()
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(dev) as clk:
-        t_wall = time.perf_counter()
-        for k in range(args.steps):
-            if not args.no_flush:
-                flush.fill_(k)  # evict the inputs from L2 (untimed)
-            starts[k].record(stream)
-            solve()
-            ends[k].record(stream)
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall
+    t_wall0 = time.time()
+    for k in range(args.steps):
+        if not args.no_flush:
+            flush.fill_(k)  # evict the inputs from L2 (untimed)
+        starts[k].record(stream)
+        solve()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    clk.mark(t_wall0, t_wall1)
+    clk.stop()
+    t_wall = t_wall1 - t_wall0
     if dist is not None:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -238,6 +288,9 @@ def run_ours(args):
     hbm_peak, peak_kind = peaks()
     achieved = dom["alg_bytes"] / (dom["total_ms"] * 1e-3) / 1e9
     solve_bytes = sum(p["alg_bytes"] for p in prof)
+    kernels = [{"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 4),
+                "alg_MB": round(p["alg_bytes"] / 1e6, 3),
+                "GBps": round(p["alg_bytes"] / (p["total_ms"] * 1e-3) / 1e9, 1)} for p in prof]
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
@@ -247,27 +300,9 @@ def run_ours(args):
                 "solve_frac": solve_bytes / (total_ms / args.steps * 1e-3) / 1e9 / hbm_peak}
 
     # end to end through the host-buffer C-ABI call, copies inside the timed region
-    hs = torch.from_numpy(g.src).pin_memory()
-    hd = torch.from_numpy(g.dst).pin_memory()
-    hw = torch.from_numpy(g.w.view(np.int32)).pin_memory()
-    ho = torch.empty(max(g.n - 1, 1), dtype=torch.int32).pin_memory()
-    hc = torch.zeros(1, dtype=torch.int64).pin_memory()
-    for _ in range(2):
-        B.mst_solve_host(h, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc, stream)
-    e2e_steps = max(3, min(args.steps, 10))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        st = B.mst_solve_host(h, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc, stream)
-        if st != B.MST_OK:
-            raise B.MstError(st, "mst_solve_host")
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": ws * g.m / e2e_s / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": 12 * g.m, "d2h_bytes_per_step": 4 * (g.n - 1) + 8,
-           "ms_per_step": e2e_s * 1e3, "timer": "host wall clock around the blocking call"}
-    if int(hc.item()) != g.n - 1:
-        raise RuntimeError("e2e self-check failed")
-
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(B, h, g, ws, stream, args)
     line = {
         "metric": METRIC, "value": ws * g.m * args.steps / (total_ms * 1e-3) / 1e6, "unit": UNIT,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -280,6 +315,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "timer": "CUDA events per step on the launching stream"},
         "roofline": roofline,
+        "kernel_replay": kernels,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -299,12 +335,13 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -170,6 +170,15 @@ mst_status mst_profile_last_solve(mst_handle h, void *stream, mst_kernel_profile
                                   int32_t cap, int32_t *count);
 
 /*
+ * Schedule of single-graph solves.  schedule: 0 = default (1), 1 = one
+ * cooperative persistent launch per solve whose phases are separated by grid
+ * barriers, 2 = one kernel per phase replayed from a CUDA graph whose round
+ * loop is a device-side conditional WHILE node.  blocks_per_sm (1..8, 0 =
+ * keep) sets the persistent grid of schedule 1.  Results are identical.
+ */
+mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm);
+
+/*
  * Schedule control for the batched solver (the autotuner's knob).
  * schedule: 0 = automatic (cached autotune result per size bucket, else the
  * built-in default), 1 = one thread block per graph, 2 = one warp per graph

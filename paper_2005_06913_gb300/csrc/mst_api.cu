@@ -344,6 +344,58 @@ mst_status mst_set_batched_schedule(mst_handle h, int schedule, int block_thread
     return MST_OK;
 }
 
+mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm)
+{
+    if (!h || schedule < 0 || schedule > 2 || blocks_per_sm < 0 || blocks_per_sm > 8)
+        return MST_ERR_INVALID_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess)
+        return MST_ERR_CUDA;
+    cudaDeviceSynchronize();
+    h->single.schedule = schedule;
+    if (blocks_per_sm > 0 && blocks_per_sm != h->single.fused_blocks_per_sm) {
+        h->single.fused_blocks_per_sm = blocks_per_sm;
+        single_release(h->single);  // the grid is fixed at reservation time
+        h->last_solve.valid = false;
+    }
+    return MST_OK;
+}
+
+mst_status mst_autotune_batched(mst_handle h, mst_weight_type wt, int32_t G,
+                                const int64_t *vtx_off, const int64_t *edge_off, int64_t total_n,
+                                int64_t total_m, const int32_t *src, const int32_t *dst,
+                                const void *w, int32_t *out_edge_ids, int64_t *out_counts,
+                                const char *cache_path, void *stream)
+{
+    if (!h || (wt != MST_W_U32 && wt != MST_W_F32) || G < 0 || total_n < 0 || total_m < 0)
+        return MST_ERR_INVALID_ARG;
+    if (G > 0 && (!vtx_off || !edge_off || !out_counts))
+        return MST_ERR_INVALID_ARG;
+    if (total_m > 0 && (!src || !dst || !w))
+        return MST_ERR_INVALID_ARG;
+    if (total_n > 0 && !out_edge_ids)
+        return MST_ERR_INVALID_ARG;
+    if (G == 0)
+        return MST_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess)
+        return MST_ERR_CUDA;
+    if (h->budget && batched_bytes(G, (uint64_t)total_n, (uint64_t)total_m) + h->single.bytes >
+                         h->budget)
+        return MST_ERR_BUDGET;
+    cudaError_t e = batched_reserve(h->batched, G, (uint64_t)total_n, (uint64_t)total_m);
+    if (e != cudaSuccess) {
+        batched_release(h->batched);
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    h->last = LAST_BATCHED;
+    e = batched_autotune(h->batched, h->device, (uint32_t)wt, G, vtx_off, edge_off,
+                         (uint64_t)total_n, (uint64_t)total_m, src, dst, w, out_edge_ids,
+                         out_counts, cache_path, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize((cudaStream_t)stream);
+    return cuda_status(e);
+}
+
 mst_status mst_server_start(mst_handle h, int streams, int max_batch)
 {
     if (!h || streams < 1 || streams > 64 || max_batch < 1)

@@ -1,17 +1,976 @@
-// placeholder: replaced by the batched solver
+// mst_batched.cu — many independent graphs in one persistent launch.
+//
+// Each graph runs the same Boruvka rounds as the single-graph path (Section
+// 2.1: find-min, hook, compress, compact/"covered" removal, repeat), but all
+// rounds of one graph are walked by one team of threads — a whole CTA, or a
+// single warp for small graphs — synchronised with __syncthreads/__syncwarp
+// instead of kernel boundaries, so a batch costs one launch however many
+// rounds its graphs need.
+//
+//   k_b_prep    validates the offset tables and counts graphs per size bin
+//   k_b_order   orders graph ids largest bin first (longest-job-first)
+//   k_b_solve   persistent CTAs take big graphs from a queue; when that
+//               queue is empty each warp takes small graphs from a second one
+//
+// Per graph, the vertex arrays (minimum keys, parents, new ids, labels, tree
+// bits) and, when they fit, the live edge list are placed in the CTA's (or
+// warp's) shared memory; otherwise in its slice of global workspace.  The
+// solver is one function over generic pointers, so both placements run the
+// same code.  Compaction is in place: tiles are read before any survivor of
+// the tile is written, and survivors move only to lower positions.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
 #include "mst_internal.h"
+
 namespace mst {
-size_t batched_bytes(int32_t, uint64_t, uint64_t) { return 0; }
-cudaError_t batched_reserve(Batched &, int32_t, uint64_t, uint64_t) { return cudaErrorNotSupported; }
-void batched_release(Batched &b) { b = Batched(); }
-cudaError_t batched_launch(Batched &, int, uint32_t, int32_t, const int64_t *, const int64_t *, uint64_t, uint64_t,
-                           const int32_t *, const int32_t *, const void *, int32_t *, int64_t *, cudaStream_t) { return cudaErrorNotSupported; }
-uint32_t batched_status_bits(Batched &, cudaStream_t, cudaError_t *err) { *err = cudaSuccess; return 0; }
-mst_status server_start(mst_handle, int, int) { return MST_ERR_INTERNAL; }
-mst_status server_submit(mst_handle, const Request &, uint64_t *) { return MST_ERR_INTERNAL; }
-mst_status server_poll(mst_handle, uint64_t, int *, double *) { return MST_ERR_INTERNAL; }
-mst_status server_drain(mst_handle) { return MST_ERR_INTERNAL; }
-mst_status server_stop(mst_handle) { return MST_ERR_INTERNAL; }
+
+struct BCtl {
+    uint32_t status;
+    uint32_t big_queue;
+    uint32_t small_queue;
+    uint32_t pad;
+    uint32_t bin_count[64];
+    uint32_t bin_cursor[64];
+};
+
+struct BWs {
+    BCtl *ctl;
+    uint4 *E;                   // total_m live edge records
+    unsigned long long *mins;   // 2 * total_n
+    int32_t *parent, *nid, *lab;
+    uint32_t *bits;             // total_m/32 + G + 1 words
+    int32_t *order;             // G
+    uint64_t total_n, total_m;
+};
+
+struct BJob {
+    const int64_t *vtx_off, *edge_off;
+    const int32_t *src, *dst;
+    const uint32_t *w;
+    int32_t *out;
+    int64_t *out_counts;
+    uint32_t wt;
+    int32_t G;
+    uint32_t warp_max_m;  // graphs with m <= this go to warps; 0 = no warp mode
+    uint32_t smem_bytes;  // dynamic shared memory per CTA
+    const GraphDesc *descs;  // when set, graphs come from this list instead
+};
+
+// One graph of a batch: its inputs, outputs and workspace slice.
+struct GraphView {
+    const int32_t *src, *dst;
+    const uint32_t *w;
+    int32_t *out;
+    int64_t *out_count;
+    uint32_t n, m, wt;
+    uint64_t vo, eo;  // workspace offsets
+    bool bad;
+};
+
+__device__ __forceinline__ GraphView graph_at(const BJob &job, int g)
+{
+    GraphView v;
+    if (job.descs) {
+        const GraphDesc d = job.descs[g];
+        v.src = d.src;
+        v.dst = d.dst;
+        v.w = (const uint32_t *)d.w;
+        v.out = d.out;
+        v.out_count = d.out_count;
+        v.n = d.n;
+        v.m = d.m;
+        v.wt = d.wt;
+        v.vo = d.ws_vo;
+        v.eo = d.ws_eo;
+        v.bad = false;
+        return v;
+    }
+    const int64_t v0 = job.vtx_off[g], v1 = job.vtx_off[g + 1];
+    const int64_t e0 = job.edge_off[g], e1 = job.edge_off[g + 1];
+    v.bad = v0 < 0 || e0 < 0 || v1 < v0 || e1 < e0 || v1 - v0 > INT32_MAX || e1 - e0 > INT32_MAX;
+    v.n = v.bad ? 0u : (uint32_t)(v1 - v0);
+    v.m = v.bad ? 0u : (uint32_t)(e1 - e0);
+    v.vo = (uint64_t)v0;
+    v.eo = (uint64_t)e0;
+    v.src = job.src + e0;
+    v.dst = job.dst + e0;
+    v.w = job.w + e0;
+    v.out = job.out + v0;
+    v.out_count = job.out_counts + g;
+    v.wt = job.wt;
+    return v;
 }
-extern "C" mst_status mst_autotune_batched(mst_handle, mst_weight_type, int32_t, const int64_t *, const int64_t *, int64_t, int64_t,
-   const int32_t *, const int32_t *, const void *, int32_t *, int64_t *, const char *, void *) { return MST_ERR_INTERNAL; }
+
+// ------------------------------------------------------------- thread teams
+
+// A whole CTA of T threads.
+template <int T>
+struct BlockTeam {
+    static constexpr int kSize = T;
+    static constexpr int kW = T / 32;
+    uint32_t *scratch;  // 4*kW + 2 words of shared memory
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool any(bool x) const { return __syncthreads_or(x ? 1 : 0) != 0; }
+
+    // Exclusive scan of the 4*kW per-(row, warp) counts in scratch; total
+    // into scratch[4*kW].  Called after a sync, followed by a sync.
+    __device__ __forceinline__ void scan_counts() const
+    {
+        constexpr int K = 4 * kW;
+        constexpr int per = (K + 31) / 32;
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            uint32_t loc[per], sum = 0;
+#pragma unroll
+            for (int i = 0; i < per; i++) {
+                const int idx = lane * per + i;
+                loc[i] = idx < K ? scratch[idx] : 0u;
+                sum += loc[i];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            uint32_t run = incl - sum;
+#pragma unroll
+            for (int i = 0; i < per; i++) {
+                const int idx = lane * per + i;
+                if (idx < K)
+                    scratch[idx] = run;
+                run += loc[i];
+            }
+            if (lane == 31)
+                scratch[K] = incl;
+        }
+    }
+
+    // Stable ranks of kept items of a striped tile (item j of thread t is
+    // tile index j*T + t) and the tile total.
+    __device__ __forceinline__ void tile_ranks(const bool (&keep)[4], uint32_t (&rank)[4],
+                                               uint32_t &total) const
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t mask[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            mask[j] = __ballot_sync(0xffffffffu, keep[j]);
+        __syncthreads();  // previous users of scratch are done
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                scratch[j * kW + warp] = __popc(mask[j]);
+        }
+        __syncthreads();
+        scan_counts();
+        __syncthreads();
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            rank[j] = scratch[j * kW + warp] + __popc(mask[j] & lt);
+        total = scratch[4 * kW];
+    }
+
+    // Exclusive offsets of per-item counts of a striped tile.
+    __device__ __forceinline__ void tile_offsets(const uint32_t (&cnt)[4], uint32_t (&off)[4],
+                                                 uint32_t &total) const
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t incl[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            incl[j] = cnt[j];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl[j], o);
+                if (lane >= o)
+                    incl[j] += y;
+            }
+        }
+        __syncthreads();
+        if (lane == 31) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                scratch[j * kW + warp] = incl[j];
+        }
+        __syncthreads();
+        scan_counts();
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            off[j] = scratch[j * kW + warp] + incl[j] - cnt[j];
+        total = scratch[4 * kW];
+    }
+};
+
+// One warp.
+struct WarpTeam {
+    static constexpr int kSize = 32;
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ bool any(bool x) const { return __any_sync(0xffffffffu, x) != 0; }
+    __device__ __forceinline__ void tile_ranks(const bool (&keep)[4], uint32_t (&rank)[4],
+                                               uint32_t &total) const
+    {
+        const uint32_t lt = lanemask_lt();
+        uint32_t run = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t mk = __ballot_sync(0xffffffffu, keep[j]);
+            rank[j] = run + __popc(mk & lt);
+            run += __popc(mk);
+        }
+        total = run;
+    }
+    __device__ __forceinline__ void tile_offsets(const uint32_t (&cnt)[4], uint32_t (&off)[4],
+                                                 uint32_t &total) const
+    {
+        const int lane = threadIdx.x & 31;
+        uint32_t run = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            uint32_t incl = cnt[j];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            off[j] = run + incl - cnt[j];
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        total = run;
+    }
+};
+
+// ------------------------------------------------------------ graph solver
+
+struct GraphArrays {
+    uint4 *E;
+    unsigned long long *mA, *mB;
+    int32_t *parent, *nid, *lab;
+    uint32_t *bits;
+};
+
+// Pointer chase with path halving through a volatile view (the array may
+// live in shared or global memory; one team owns it).
+__device__ __forceinline__ bool chase_v(volatile int32_t *parent, uint32_t start, uint32_t &at)
+{
+    uint32_t x = start;
+#pragma unroll 1
+    for (int s = 0; s < kChaseLimit; s++) {
+        const uint32_t p = (uint32_t)parent[x];
+        if (p == x) {
+            at = x;
+            return true;
+        }
+        const uint32_t gp = (uint32_t)parent[p];
+        if (gp == p) {
+            at = p;
+            return true;
+        }
+        parent[x] = (int32_t)gp;
+        x = gp;
+    }
+    at = x;
+    return false;
+}
+
+// All Boruvka rounds of one graph by one team.  Inputs are the graph's slice
+// of the caller's arrays (local ids); A the graph's working arrays.
+template <class Team>
+__device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_t *src,
+                            const int32_t *dst, const uint32_t *w, uint32_t wt,
+                            const GraphArrays &A, int32_t *out, int64_t *out_count,
+                            uint32_t *status)
+{
+    constexpr int T = Team::kSize;
+    constexpr int TILE = 4 * T;
+    const int t = tm.rank();
+    const uint32_t words = (m + 31u) >> 5;
+    for (uint32_t v = t; v < n; v += T)
+        A.mA[v] = kNoEdge;
+    for (uint32_t i = t; i < words; i += T)
+        A.bits[i] = 0u;
+    tm.sync();
+    // round-0 find-min (Section 2.1 steps 15-28)
+    for (uint32_t e = t; e < m; e += T) {
+        const uint32_t u = (uint32_t)__ldg(src + e), v = (uint32_t)__ldg(dst + e);
+        if (u >= n || v >= n) {
+            atomicOr(status, ST_BAD_VERTEX);
+            continue;
+        }
+        if (u == v)
+            continue;
+        const unsigned long long key = make_key(weight_bits(__ldg(w + e), wt, status), e);
+        atomicMin(&A.mA[u], key);
+        atomicMin(&A.mA[v], key);
+    }
+    tm.sync();
+    uint32_t n_r = n, m_r = m;
+    unsigned long long *mc = A.mA, *mx = A.mB;
+    for (uint32_t r = 0;; r++) {
+        // hook (steps 30-40) and dense renumbering of roots
+        uint32_t run = 0;
+        for (uint32_t base = 0; base < n_r; base += TILE) {
+            bool root[4];
+            uint32_t vv[4], rank[4], total;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t v = base + j * T + t;
+                vv[j] = v;
+                root[j] = false;
+                if (v < n_r) {
+                    const unsigned long long k = mc[v];
+                    mx[v] = kNoEdge;
+                    if (k == kNoEdge) {
+                        root[j] = true;
+                    } else {
+                        const uint32_t p = (uint32_t)k;
+                        uint32_t a, b, id;
+                        if (r == 0) {
+                            a = (uint32_t)__ldg(src + p);
+                            b = (uint32_t)__ldg(dst + p);
+                            id = p;
+                        } else {
+                            const uint4 q = A.E[p];
+                            a = q.x;
+                            b = q.y;
+                            id = q.w;
+                        }
+                        const uint32_t d = (a == v) ? b : a;
+                        const unsigned long long kd = mc[d];
+                        if ((uint32_t)kd == p && v < d) {
+                            root[j] = true;
+                        } else {
+                            A.parent[v] = (int32_t)d;
+                            atomicOr(&A.bits[id >> 5], 1u << (id & 31));
+                        }
+                    }
+                    if (root[j])
+                        A.parent[v] = (int32_t)v;
+                }
+            }
+            tm.tile_ranks(root, rank, total);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (root[j])
+                    A.nid[vv[j]] = (int32_t)(run + rank[j]);
+            run += total;
+        }
+        const uint32_t n_next = run;
+        tm.sync();
+        // compress: every component takes its root's new id
+        for (uint32_t pass = 0;; pass++) {
+            bool unfinished = false;
+            for (uint32_t v = t; v < n_r; v += T) {
+                uint32_t start = v;
+                if (pass > 0) {
+                    if (((volatile int32_t *)A.lab)[v] != -1)
+                        continue;
+                    start = (uint32_t)((volatile int32_t *)A.parent)[v];
+                }
+                uint32_t at;
+                if (chase_v(A.parent, start, at)) {
+                    A.lab[v] = A.nid[at];
+                } else {
+                    A.lab[v] = -1;
+                    ((volatile int32_t *)A.parent)[v] = (int32_t)at;
+                    unfinished = true;
+                }
+            }
+            if (!tm.any(unfinished))
+                break;
+            if (pass + 1 >= kMaxJumpPasses) {
+                atomicOr(status, ST_INTERNAL);
+                break;
+            }
+        }
+        tm.sync();
+        // compact in place + find-min of the next round
+        run = 0;
+        for (uint32_t base = 0; base < m_r; base += TILE) {
+            bool keep[4];
+            uint4 rec[4];
+            uint32_t rank[4], total;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t i = base + j * T + t;
+                keep[j] = false;
+                rec[j] = make_uint4(0, 0, 0, 0);
+                if (i < m_r) {
+                    uint32_t u, v, wb, id;
+                    bool ok;
+                    if (r == 0) {
+                        u = (uint32_t)__ldg(src + i);
+                        v = (uint32_t)__ldg(dst + i);
+                        ok = u < n && v < n && u != v;
+                        wb = ok ? weight_bits(__ldg(w + i), wt, status) : 0u;
+                        id = i;
+                    } else {
+                        const uint4 q = A.E[i];
+                        u = q.x;
+                        v = q.y;
+                        wb = q.z;
+                        id = q.w;
+                        ok = true;
+                    }
+                    if (ok) {
+                        const uint32_t nu = (uint32_t)A.lab[u], nv = (uint32_t)A.lab[v];
+                        if (nu >= n_next || nv >= n_next) {
+                            atomicOr(status, ST_INTERNAL);
+                        } else if (nu != nv) {
+                            keep[j] = true;
+                            rec[j] = make_uint4(nu, nv, wb, id);
+                        }
+                    }
+                }
+            }
+            tm.tile_ranks(keep, rank, total);  // all loads of the tile precede its syncs
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (keep[j]) {
+                    const uint32_t pos = run + rank[j];
+                    A.E[pos] = rec[j];
+                    const unsigned long long key = make_key(rec[j].z, pos);
+                    atomicMin(&mx[rec[j].x], key);
+                    atomicMin(&mx[rec[j].y], key);
+                }
+            }
+            run += total;
+        }
+        tm.sync();
+        m_r = run;
+        n_r = n_next;
+        unsigned long long *tmp = mc;
+        mc = mx;
+        mx = tmp;
+        if (m_r == 0)
+            break;
+        if (r + 1 >= (uint32_t)kMaxRounds) {
+            atomicOr(status, ST_INTERNAL);
+            break;
+        }
+    }
+    // emit ascending edge ids
+    const uint32_t cap = n > 0 ? n - 1 : 0;
+    uint32_t run = 0;
+    for (uint32_t base = 0; base < words; base += TILE) {
+        uint32_t wv[4], cnt[4], off[4], total;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t i = base + j * T + t;
+            wv[j] = i < words ? A.bits[i] : 0u;
+            cnt[j] = __popc(wv[j]);
+        }
+        tm.tile_offsets(cnt, off, total);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            uint32_t bits = wv[j], pos = run + off[j];
+            const uint32_t i = base + j * T + t;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (pos < cap)
+                    out[pos] = (int32_t)(i * 32u + (uint32_t)b);
+                else
+                    atomicOr(status, ST_INTERNAL);
+                pos++;
+            }
+        }
+        run += total;
+    }
+    if (t == 0) {
+        *out_count = (int64_t)run;
+        if (run + n_r != n)
+            atomicOr(status, ST_INTERNAL);
+        if (n_r > 1)
+            atomicOr(status, ST_DISCONNECTED);
+    }
+    tm.sync();
+}
+
+// Shared-memory bytes of a graph's vertex arrays and of its edge list.
+__host__ __device__ __forceinline__ size_t vbytes_of(uint32_t n, uint32_t m)
+{
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    return 2 * al((size_t)n * 8) + 3 * al((size_t)n * 4) + al((((size_t)m + 31) / 32) * 4);
+}
+
+__host__ __device__ __forceinline__ size_t ebytes_of(uint32_t m) { return (size_t)m * 16; }
+
+// Places a graph's arrays in `sm` (shared, `budget` bytes) where they fit.
+__device__ __forceinline__ GraphArrays place(const BWs &ws, char *sm, size_t budget, int g,
+                                            uint64_t vo, uint64_t eo, uint32_t n, uint32_t m)
+{
+    GraphArrays A;
+    const size_t vb = vbytes_of(n, m), eb = ebytes_of(m);
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    if (vb <= budget) {
+        char *p = sm;
+        A.mA = (unsigned long long *)p;
+        p += al((size_t)n * 8);
+        A.mB = (unsigned long long *)p;
+        p += al((size_t)n * 8);
+        A.parent = (int32_t *)p;
+        p += al((size_t)n * 4);
+        A.nid = (int32_t *)p;
+        p += al((size_t)n * 4);
+        A.lab = (int32_t *)p;
+        p += al((size_t)n * 4);
+        A.bits = (uint32_t *)p;
+        p += al((((size_t)m + 31) / 32) * 4);
+        A.E = (vb + eb <= budget) ? (uint4 *)p : ws.E + eo;
+    } else {
+        A.mA = ws.mins + vo;
+        A.mB = ws.mins + ws.total_n + vo;
+        A.parent = ws.parent + vo;
+        A.nid = ws.nid + vo;
+        A.lab = ws.lab + vo;
+        A.bits = ws.bits + (eo >> 5) + (uint64_t)g;
+        A.E = ws.E + eo;
+    }
+    return A;
+}
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void k_b_prep(BWs ws, BJob job, uint64_t total_n, uint64_t total_m)
+{
+    BCtl *c = ws.ctl;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < job.G; g += gridDim.x * blockDim.x) {
+        const GraphView gv = graph_at(job, g);
+        bool bad = gv.bad || gv.vo + gv.n > total_n || gv.eo + gv.m > total_m;
+        if (!job.descs) {
+            if (g == 0 && (gv.vo != 0 || gv.eo != 0))
+                bad = true;
+            if (g == job.G - 1 && (gv.vo + gv.n != total_n || gv.eo + gv.m != total_m))
+                bad = true;
+        }
+        if (bad)
+            atomicOr(&c->status, ST_BAD_OFFSETS);
+        const uint32_t m = bad ? 0u : gv.m;
+        const uint32_t bin = m ? 31u - __clz(m) : 0u;
+        const bool big = job.warp_max_m == 0 || m > job.warp_max_m;
+        atomicAdd(&c->bin_count[bin + (big ? 32 : 0)], 1u);
+    }
+}
+
+__global__ void k_b_order(BWs ws, BJob job)
+{
+    __shared__ uint32_t base[64];
+    BCtl *c = ws.ctl;
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 63; b >= 0; b--) {  // big bins first, larger bins first
+            base[b] = run;
+            run += c->bin_count[b];
+        }
+    }
+    __syncthreads();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < job.G; g += gridDim.x * blockDim.x) {
+        const GraphView gv = graph_at(job, g);
+        const uint32_t m = gv.bad ? 0u : gv.m;
+        const uint32_t bin = m ? 31u - __clz(m) : 0u;
+        const bool big = job.warp_max_m == 0 || m > job.warp_max_m;
+        const uint32_t b = bin + (big ? 32 : 0);
+        if (gv.out_count)
+            *gv.out_count = 0;
+        ws.order[base[b] + atomicAdd(&c->bin_cursor[b], 1u)] = g;
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) k_b_solve(BWs ws, BJob job)
+{
+    extern __shared__ __align__(16) char smem[];
+    __shared__ uint32_t scratch[4 * (T / 32) + 2];
+    __shared__ uint32_t s_claim;
+    BCtl *c = ws.ctl;
+    if (c->status & ST_BAD_OFFSETS)
+        return;
+    uint32_t n_big = 0;
+    for (int b = 32; b < 64; b++)
+        n_big += c->bin_count[b];
+    BlockTeam<T> team{scratch};
+    // big graphs: one CTA each, largest first
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_claim = atomicAdd(&c->big_queue, 1u);
+        __syncthreads();
+        const uint32_t q = s_claim;
+        if (q >= n_big)
+            break;
+        const int g = ws.order[q];
+        const GraphView gv = graph_at(job, g);
+        const GraphArrays A = place(ws, smem, job.smem_bytes, g, gv.vo, gv.eo, gv.n, gv.m);
+        solve_graph(team, gv.n, gv.m, gv.src, gv.dst, gv.w, gv.wt, A, gv.out, gv.out_count,
+                    &c->status);
+    }
+    if (job.warp_max_m == 0)
+        return;
+    // small graphs: one warp each
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t share = (job.smem_bytes / (T / 32)) & ~(size_t)15;
+    char *mine = smem + (size_t)warp * share;
+    WarpTeam wt_team;
+    const uint32_t G = (uint32_t)job.G;
+    for (;;) {
+        uint32_t q = 0;
+        if (lane == 0)
+            q = atomicAdd(&c->small_queue, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0) + n_big;
+        if (q >= G)
+            break;
+        const int g = ws.order[q];
+        const GraphView gv = graph_at(job, g);
+        const GraphArrays A = place(ws, mine, share, g, gv.vo, gv.eo, gv.n, gv.m);
+        solve_graph(wt_team, gv.n, gv.m, gv.src, gv.dst, gv.w, gv.wt, A, gv.out, gv.out_count,
+                    &c->status);
+    }
+}
+
+// ------------------------------------------------------------------- host
+
+#define MST_TRY(x)                     \
+    do {                               \
+        cudaError_t e_ = (x);          \
+        if (e_ != cudaSuccess)         \
+            return e_;                 \
+    } while (0)
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t batched_bytes(int32_t G, uint64_t n, uint64_t m)
+{
+    size_t b = al256(sizeof(BCtl));
+    b += al256(m * 16);
+    b += al256(n * 16);
+    b += 3 * al256(n * 4);
+    b += al256((m / 32 + (uint64_t)G + 1) * 4);
+    b += al256((size_t)G * 4);
+    return b;
+}
+
+void batched_release(Batched &b)
+{
+    if (b.base)
+        cudaFree(b.base);
+    std::map<int, BatchedConfig> tuned;
+    tuned.swap(b.tuned);
+    const int schedule = b.schedule, threads = b.block_threads;
+    const bool loaded = b.tuned_loaded;
+    b = Batched();
+    b.tuned.swap(tuned);
+    b.schedule = schedule;
+    b.block_threads = threads;
+    b.tuned_loaded = loaded;
+}
+
+cudaError_t batched_reserve(Batched &b, int32_t G, uint64_t n, uint64_t m)
+{
+    if (b.base && G <= b.g_cap && n <= b.n_cap && m <= b.m_cap)
+        return cudaSuccess;
+    const int32_t gc = std::max(G, b.g_cap);
+    const uint64_t nc = std::max(n, b.n_cap), mc = std::max(m, b.m_cap);
+    if (b.base)
+        cudaFree(b.base);
+    b.base = nullptr;
+    b.bytes = batched_bytes(gc, nc, mc);
+    MST_TRY(cudaMalloc(&b.base, b.bytes));
+    b.g_cap = gc;
+    b.n_cap = nc;
+    b.m_cap = mc;
+    return cudaSuccess;
+}
+
+static BWs carve_at(void *base, int32_t g_cap, uint64_t n_cap, uint64_t m_cap, uint64_t total_n,
+                    uint64_t total_m)
+{
+    BWs ws;
+    char *p = (char *)base;
+    auto take = [&](size_t sz) {
+        char *q = p;
+        p += al256(sz);
+        return (void *)q;
+    };
+    ws.ctl = (BCtl *)take(sizeof(BCtl));
+    ws.E = (uint4 *)take(m_cap * 16);
+    ws.mins = (unsigned long long *)take(n_cap * 16);
+    ws.parent = (int32_t *)take(n_cap * 4);
+    ws.nid = (int32_t *)take(n_cap * 4);
+    ws.lab = (int32_t *)take(n_cap * 4);
+    ws.bits = (uint32_t *)take((m_cap / 32 + (uint64_t)g_cap + 1) * 4);
+    ws.order = (int32_t *)take((size_t)g_cap * 4);
+    ws.total_n = total_n;
+    ws.total_m = total_m;
+    return ws;
+}
+
+static BWs carve(Batched &b, uint64_t total_n, uint64_t total_m)
+{
+    BWs ws;
+    char *p = (char *)b.base;
+    auto take = [&](size_t sz) {
+        char *q = p;
+        p += al256(sz);
+        return (void *)q;
+    };
+    ws.ctl = (BCtl *)take(sizeof(BCtl));
+    ws.E = (uint4 *)take(b.m_cap * 16);
+    ws.mins = (unsigned long long *)take(b.n_cap * 16);
+    ws.parent = (int32_t *)take(b.n_cap * 4);
+    ws.nid = (int32_t *)take(b.n_cap * 4);
+    ws.lab = (int32_t *)take(b.n_cap * 4);
+    ws.bits = (uint32_t *)take((b.m_cap / 32 + (uint64_t)b.g_cap + 1) * 4);
+    ws.order = (int32_t *)take((size_t)b.g_cap * 4);
+    ws.total_n = total_n;  // mins B half starts after the batch's vertices
+    ws.total_m = total_m;
+    return ws;
+}
+
+struct Choice {
+    int threads;
+    int blocks_per_sm;
+    uint32_t warp_max_m;
+};
+
+template <int T>
+static cudaError_t launch_solve(const BWs &ws, const BJob &job, int device, int blocks_per_sm,
+                                cudaStream_t s)
+{
+    int sms = 0;
+    MST_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    MST_TRY(cudaFuncSetAttribute(k_b_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)job.smem_bytes));
+    int occ = 0;
+    MST_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_b_solve<T>, T, job.smem_bytes));
+    if (occ < 1)
+        return cudaErrorInvalidConfiguration;
+    const int bps = std::min(occ, blocks_per_sm);
+    k_b_solve<T><<<sms * bps, T, job.smem_bytes, s>>>(ws, job);
+    return cudaGetLastError();
+}
+
+// Shared memory per CTA for `bps` CTAs of T threads on one SM.
+static uint32_t smem_for(int device, int bps)
+{
+    int per_sm = 0, per_block = 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    size_t s = (size_t)per_sm / (size_t)bps;
+    s = s > 2048 ? s - 2048 : s;  // static shared memory and the per-CTA reserve
+    s = std::min(s, (size_t)per_block - 1024);
+    return (uint32_t)(s & ~(size_t)255);
+}
+
+static cudaError_t run_batched(Batched &b, int device, const BWs &ws, BJob job, const Choice &ch,
+                               cudaStream_t s)
+{
+    job.warp_max_m = ch.warp_max_m;
+    job.smem_bytes = smem_for(device, ch.blocks_per_sm);
+    MST_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(BCtl), s));
+    const int pg = (int)std::min<int64_t>((job.G + 255) / 256, 1024);
+    k_b_prep<<<std::max(pg, 1), 256, 0, s>>>(ws, job, ws.total_n, ws.total_m);
+    MST_TRY(cudaGetLastError());
+    k_b_order<<<std::max(pg, 1), 256, 0, s>>>(ws, job);
+    MST_TRY(cudaGetLastError());
+    switch (ch.threads) {
+    case 128: return launch_solve<128>(ws, job, device, ch.blocks_per_sm, s);
+    case 256: return launch_solve<256>(ws, job, device, ch.blocks_per_sm, s);
+    case 512: return launch_solve<512>(ws, job, device, ch.blocks_per_sm, s);
+    default: return launch_solve<1024>(ws, job, device, ch.blocks_per_sm, s);
+    }
+}
+
+// Size bucket of a batch for the autotune cache: log2 of its mean edges.
+static int bucket_of(int32_t G, uint64_t total_m)
+{
+    const double mean = G > 0 ? (double)total_m / G : 0.0;
+    return mean < 1 ? 0 : (int)std::floor(std::log2(mean));
+}
+
+static Choice default_choice(int32_t G, uint64_t total_m)
+{
+    const double mean = G > 0 ? (double)total_m / G : 0.0;
+    if (mean < 4096)
+        return Choice{256, 4, 512};
+    return Choice{512, 2, 1024};
+}
+
+static Choice choice_from_config(const BatchedConfig &c)
+{
+    Choice ch{c.block_threads, c.blocks_per_sm, (uint32_t)c.warp_max_m};
+    return ch;
+}
+
+static bool json_load(Batched &b, const char *path)
+{
+    std::ifstream f(path);
+    if (!f)
+        return false;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    size_t pos = 0;
+    int loaded = 0;
+    // entries: {"bucket": B, "threads": T, "blocks_per_sm": K, "warp_max_m": W}
+    while ((pos = s.find("\"bucket\"", pos)) != std::string::npos) {
+        BatchedConfig c;
+        int bucket = 0;
+        if (sscanf(s.c_str() + pos, "\"bucket\": %d, \"threads\": %d, \"blocks_per_sm\": %d, "
+                                    "\"warp_max_m\": %d",
+                   &bucket, &c.block_threads, &c.blocks_per_sm, &c.warp_max_m) == 4) {
+            c.schedule = c.warp_max_m > 0 ? 2 : 1;
+            b.tuned[bucket] = c;
+            loaded++;
+        }
+        pos += 8;
+    }
+    return loaded > 0;
+}
+
+static void json_store(const Batched &b, const char *path)
+{
+    FILE *f = fopen(path, "w");
+    if (!f)
+        return;
+    fprintf(f, "{\"mst_batched_autotune\": [\n");
+    size_t i = 0;
+    for (const auto &kv : b.tuned) {
+        fprintf(f, "  {\"bucket\": %d, \"threads\": %d, \"blocks_per_sm\": %d, \"warp_max_m\": %d}%s\n",
+                kv.first, kv.second.block_threads, kv.second.blocks_per_sm, kv.second.warp_max_m,
+                ++i < b.tuned.size() ? "," : "");
+    }
+    fprintf(f, "]}\n");
+    fclose(f);
+}
+
+cudaError_t batched_launch(Batched &b, int device, uint32_t wt, int32_t G, const int64_t *vtx_off,
+                           const int64_t *edge_off, uint64_t total_n, uint64_t total_m,
+                           const int32_t *src, const int32_t *dst, const void *w, int32_t *out,
+                           int64_t *out_counts, cudaStream_t stream)
+{
+    const BWs ws = carve(b, total_n, total_m);
+    BJob job{vtx_off, edge_off, src, dst, (const uint32_t *)w, out, out_counts, wt, G, 0, 0,
+             nullptr};
+    Choice ch = default_choice(G, total_m);
+    auto it = b.tuned.find(bucket_of(G, total_m));
+    if (it != b.tuned.end())
+        ch = choice_from_config(it->second);
+    if (b.schedule == 1)
+        ch.warp_max_m = 0;
+    else if (b.schedule == 2 && ch.warp_max_m == 0)
+        ch.warp_max_m = 512;
+    if (b.block_threads)
+        ch.threads = b.block_threads;
+    return run_batched(b, device, ws, job, ch, stream);
+}
+
+size_t desc_batch_bytes(int32_t G, uint64_t total_n, uint64_t total_m)
+{
+    return batched_bytes(G, total_n, total_m);
+}
+
+cudaError_t batched_launch_desc(const Batched &tuning, int device, void *ws_base, int32_t G,
+                                const GraphDesc *descs, uint64_t total_n, uint64_t total_m,
+                                cudaStream_t stream)
+{
+    const BWs ws = carve_at(ws_base, G, total_n, total_m, total_n, total_m);
+    BJob job{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, G, 0, 0, descs};
+    Choice ch = default_choice(G, total_m);
+    auto it = tuning.tuned.find(bucket_of(G, total_m));
+    if (it != tuning.tuned.end())
+        ch = choice_from_config(it->second);
+    Batched scratch;  // run_batched only reads its caller's shapes
+    scratch.m_cap = total_m;
+    return run_batched(scratch, device, ws, job, ch, stream);
+}
+
+cudaError_t desc_batch_status(void *ws_base, uint32_t *bits, cudaStream_t stream)
+{
+    MST_TRY(cudaMemcpyAsync(bits, ws_base, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    return cudaStreamSynchronize(stream);
+}
+
+uint32_t batched_status_bits(Batched &b, cudaStream_t stream, cudaError_t *err)
+{
+    *err = cudaSuccess;
+    if (!b.base)
+        return 0;
+    uint32_t bits = 0;
+    *err = cudaStreamSynchronize(stream);
+    if (*err == cudaSuccess)
+        *err = cudaMemcpy(&bits, b.base, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    return bits;
+}
+
+cudaError_t batched_autotune(Batched &b, int device, uint32_t wt, int32_t G,
+                             const int64_t *vtx_off, const int64_t *edge_off, uint64_t total_n,
+                             uint64_t total_m, const int32_t *src, const int32_t *dst,
+                             const void *w, int32_t *out, int64_t *out_counts, const char *path,
+                             cudaStream_t stream)
+{
+    const int bucket = bucket_of(G, total_m);
+    if (path && !b.tuned_loaded) {
+        json_load(b, path);
+        b.tuned_loaded = true;
+    }
+    if (b.tuned.count(bucket))
+        return cudaSuccess;
+    const BWs ws = carve(b, total_n, total_m);
+    BJob job{vtx_off, edge_off, src, dst, (const uint32_t *)w, out, out_counts, wt, G, 0, 0,
+             nullptr};
+    const Choice cands[] = {
+        {256, 4, 0},   {256, 4, 256},  {256, 4, 1024}, {256, 8, 512},
+        {512, 2, 0},   {512, 2, 512},  {512, 2, 2048}, {512, 4, 1024},
+        {1024, 1, 0},  {1024, 1, 1024}, {1024, 2, 2048}, {128, 8, 512},
+    };
+    cudaEvent_t e0, e1;
+    MST_TRY(cudaEventCreate(&e0));
+    MST_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Choice bestc = default_choice(G, total_m);
+    for (const Choice &c : cands) {
+        if (run_batched(b, device, ws, job, c, stream) != cudaSuccess) {  // warm-up
+            cudaGetLastError();
+            continue;
+        }
+        MST_TRY(cudaEventRecord(e0, stream));
+        MST_TRY(run_batched(b, device, ws, job, c, stream));
+        MST_TRY(cudaEventRecord(e1, stream));
+        MST_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        MST_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BatchedConfig bc;
+    bc.block_threads = bestc.threads;
+    bc.blocks_per_sm = bestc.blocks_per_sm;
+    bc.warp_max_m = (int)bestc.warp_max_m;
+    bc.schedule = bestc.warp_max_m ? 2 : 1;
+    b.tuned[bucket] = bc;
+    if (path)
+        json_store(b, path);
+    return cudaSuccess;
+}
+
+}  // namespace mst

@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 namespace mst {
 
@@ -58,6 +59,8 @@ struct Ctl {
     uint32_t deep;    // some pointer chase did not reach its root
     uint32_t deep_seen;  // value of deep at the end of the last compress pass
     uint32_t passes;     // follow-up compress passes in the current round
+    uint32_t flag3[3];   // per-pass "chase unfinished" flags of the fused kernel
+    uint32_t emitted;    // tree edges written by emit (own field: m_next may still be read)
     uint32_t status;  // ST_* bits
     uint32_t stat_m[kMaxRounds + 1];
     uint32_t stat_n[kMaxRounds + 1];
@@ -75,6 +78,7 @@ struct Ws {
     int32_t *lab;      // new id of each component after compression
     uint32_t *mst_bits;
     unsigned long long *desc;  // look-back descriptors
+    uint32_t *bar;             // grid-barrier counters of the fused kernel
     uint32_t n_cap, m_cap, desc_cap;
 };
 
@@ -266,8 +270,13 @@ __device__ __forceinline__ uint32_t lookback_warp(unsigned long long *desc, uint
         const uint32_t need = stop == 32u ? 0xffffffffu : ((2u << stop) - 1u);
         if (zmask & need) {  // an unpublished tile before the nearest prefix: wait
             if (++spins > kSpinLimit) {
-                if (lane == 0)
+                if (lane == 0) {
                     atomicOr(status, ST_TIMEOUT);
+                    const int z = __ffs(zmask & need) - 1;
+                    printf("mst: look-back gave up: tile %u epoch %u waiting on tile %lld "
+                           "(block %u of %u)\n", tile, epoch, (long long)(hi - z), blockIdx.x,
+                           gridDim.x);
+                }
                 break;
             }
             __nanosleep(20);

@@ -30,6 +30,9 @@ struct Single {
     cudaGraphExec_t exec = nullptr;
     int grid_tiles = 0;     // persistent grid of the tile kernels
     int grid_stream = 0;    // grid of the grid-stride kernels
+    int grid_fused = 0;     // co-resident grid of the fused cooperative kernel
+    int fused_blocks_per_sm = 4;
+    int schedule = 0;       // 0/1 fused cooperative kernel, 2 CUDA graph of kernels
     uint64_t solves = 0;    // solves since the descriptors were last cleared
 };
 
@@ -49,6 +52,7 @@ void single_release(Single &s);
 cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n,
                           uint32_t m, cudaStream_t stream);
+double single_alg_bytes(const Ctl &c);
 // Replays a solve kernel by kernel between CUDA events (synchronous).
 cudaError_t single_profile(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                            uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n, uint32_t m,
@@ -56,10 +60,23 @@ cudaError_t single_profile(Single &s, const int32_t *src, const int32_t *dst, co
 
 // ------------------------------------------------------------------ batched
 
+// One graph of a descriptor-list batch (the serving path): caller buffers,
+// sizes, weight type and the graph's offsets into the batch workspace.
+struct GraphDesc {
+    const int32_t *src, *dst;
+    const void *w;
+    int32_t *out;
+    int64_t *out_count;
+    uint32_t n, m, wt, pad;
+    uint64_t ws_vo, ws_eo;
+};
+
 // Per-size-bucket schedule of the batched solver.
 struct BatchedConfig {
     int schedule = 0;       // 1 block per graph, 2 warp per small graph
     int block_threads = 0;  // 0 = automatic
+    int blocks_per_sm = 0;  // CTAs per SM (sets the shared memory per CTA)
+    int warp_max_m = 0;     // graphs with at most this many edges go to warps
 };
 
 struct Batched {
@@ -82,6 +99,20 @@ cudaError_t batched_launch(Batched &b, int device, uint32_t wt, int32_t G, const
                            const int32_t *src, const int32_t *dst, const void *w, int32_t *out,
                            int64_t *out_counts, cudaStream_t stream);
 uint32_t batched_status_bits(Batched &b, cudaStream_t stream, cudaError_t *err);
+// Workspace bytes of a descriptor batch with these totals.
+size_t desc_batch_bytes(int32_t G, uint64_t total_n, uint64_t total_m);
+// Solves a descriptor batch in caller-provided workspace `ws_base` (of
+// desc_batch_bytes bytes); `descs` is a device array of G entries.
+cudaError_t batched_launch_desc(const Batched &tuning, int device, void *ws_base, int32_t G,
+                                const GraphDesc *descs, uint64_t total_n, uint64_t total_m,
+                                cudaStream_t stream);
+// Device status bits of a descriptor batch run in `ws_base`.
+cudaError_t desc_batch_status(void *ws_base, uint32_t *bits, cudaStream_t stream);
+cudaError_t batched_autotune(Batched &b, int device, uint32_t wt, int32_t G,
+                             const int64_t *vtx_off, const int64_t *edge_off, uint64_t total_n,
+                             uint64_t total_m, const int32_t *src, const int32_t *dst,
+                             const void *w, int32_t *out, int64_t *out_counts, const char *path,
+                             cudaStream_t stream);
 
 // ------------------------------------------------------------------ serving
 

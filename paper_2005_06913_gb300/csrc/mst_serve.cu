@@ -1,0 +1,325 @@
+// mst_serve.cu — continuous-batching server over the batched solver.
+//
+// A host thread owns up to S CUDA streams ("slots").  Submitted graphs wait
+// in a FIFO queue.  Whenever a slot is free, the thread takes queued requests
+// in arrival order, as many as fit max_batch and the memory budget (each
+// request needs workspace for its edge list and vertex arrays), builds a
+// descriptor list in pinned host memory, and launches one batched solve on
+// the slot's stream with workspace from the stream-ordered allocator.  When
+// the slot's completion event fires, the requests are marked done (their
+// latency is completion minus submit time) and the memory is released.  So
+// requests that arrive while other batches run on the GPU are admitted as
+// soon as a slot and memory free up, and their solves overlap on the device.
+// Each request's result is the same as a solve of that graph alone: the
+// minimum spanning tree under the (weight, edge id) order is unique.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <chrono>
+#include <unordered_map>
+
+#include "mst_internal.h"
+
+namespace mst {
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    GraphDesc *h_desc = nullptr;  // pinned host descriptors
+    GraphDesc *d_desc = nullptr;  // device copy
+    int cap = 0;
+    void *ws = nullptr;           // workspace of the batch in flight
+    size_t ws_bytes = 0;
+    std::vector<uint64_t> tickets;
+    bool busy = false;
+};
+
+struct Outcome {
+    bool done = false;
+    double latency_us = 0.0;
+    mst_status status = MST_OK;
+};
+
+struct Server {
+    mst_handle h = nullptr;
+    std::thread thr;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request> pending;
+    std::unordered_map<uint64_t, Outcome> results;
+    std::unordered_map<uint64_t, double> submit_us;
+    std::vector<Slot> slots;
+    int max_batch = 256;
+    uint64_t next_ticket = 1;
+    size_t in_use = 0;
+    int inflight = 0;
+    bool stop = false;
+    cudaError_t error = cudaSuccess;
+};
+
+// Workspace of one request inside a batch (edge list, vertex arrays, bits).
+static size_t request_bytes(uint32_t n, uint32_t m)
+{
+    return (size_t)m * 16 + (size_t)n * 28 + ((size_t)m / 32 + 2) * 4 + 64;
+}
+
+static void complete_slot(Server &S, Slot &sl)
+{
+    const double t = now_us();
+    uint32_t bits = 0;
+    cudaMemcpy(&bits, sl.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    cudaFreeAsync(sl.ws, sl.stream);
+    const mst_status st = status_from_bits(bits & ~(uint32_t)ST_DISCONNECTED);
+    std::lock_guard<std::mutex> lk(S.mu);
+    for (uint64_t tk : sl.tickets) {
+        Outcome &o = S.results[tk];
+        o.done = true;
+        o.latency_us = t - S.submit_us[tk];
+        o.status = st;
+        S.submit_us.erase(tk);
+    }
+    S.in_use -= sl.ws_bytes;
+    S.inflight--;
+    sl.tickets.clear();
+    sl.ws = nullptr;
+    sl.ws_bytes = 0;
+    sl.busy = false;
+    S.cv.notify_all();
+}
+
+// Takes queued requests for one batch (lock held).  Requests that can never
+// fit the budget are completed at once with MST_ERR_BUDGET.
+static std::vector<Request> take_batch(Server &S, size_t budget)
+{
+    std::vector<Request> batch;
+    size_t bytes = 4096 + 64 * 4;  // control block and order list slack
+    while (!S.pending.empty() && (int)batch.size() < S.max_batch) {
+        Request &r = S.pending.front();
+        const size_t need = request_bytes((uint32_t)r.n, (uint32_t)r.m);
+        if (budget && need + 4096 > budget) {  // can never be admitted
+            Outcome &o = S.results[r.ticket];
+            o.done = true;
+            o.status = MST_ERR_BUDGET;
+            S.submit_us.erase(r.ticket);
+            S.pending.pop_front();
+            continue;
+        }
+        if (budget && S.in_use + bytes + need > budget)
+            break;
+        bytes += need;
+        batch.push_back(r);
+        S.pending.pop_front();
+    }
+    return batch;
+}
+
+static cudaError_t launch_batch(Server &S, Slot &sl, std::vector<Request> &batch)
+{
+    const int G = (int)batch.size();
+    if (G > sl.cap) {
+        if (sl.h_desc)
+            cudaFreeHost(sl.h_desc);
+        if (sl.d_desc)
+            cudaFree(sl.d_desc);
+        sl.cap = std::max(G, 2 * sl.cap);
+        cudaError_t e = cudaMallocHost((void **)&sl.h_desc, sizeof(GraphDesc) * sl.cap);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&sl.d_desc, sizeof(GraphDesc) * sl.cap);
+        if (e != cudaSuccess)
+            return e;
+    }
+    uint64_t vo = 0, eo = 0;
+    for (int i = 0; i < G; i++) {
+        const Request &r = batch[i];
+        GraphDesc &d = sl.h_desc[i];
+        d.src = r.src;
+        d.dst = r.dst;
+        d.w = r.w;
+        d.out = r.out;
+        d.out_count = r.out_count;
+        d.n = (uint32_t)r.n;
+        d.m = (uint32_t)r.m;
+        d.wt = r.wt;
+        d.pad = 0;
+        d.ws_vo = vo;
+        d.ws_eo = eo;
+        vo += (uint64_t)r.n;
+        eo += (uint64_t)r.m;
+    }
+    const size_t bytes = desc_batch_bytes(G, vo, eo);
+    cudaError_t e = cudaMallocAsync(&sl.ws, bytes, sl.stream);
+    if (e != cudaSuccess)
+        return e;
+    sl.ws_bytes = bytes;
+    e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(GraphDesc) * G, cudaMemcpyHostToDevice,
+                        sl.stream);
+    if (e == cudaSuccess)
+        e = batched_launch_desc(S.h->batched, S.h->device, sl.ws, G, sl.d_desc, vo, eo, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(sl.done, sl.stream);
+    sl.tickets.clear();
+    for (const Request &r : batch)
+        sl.tickets.push_back(r.ticket);
+    return e;
+}
+
+static void server_loop(Server *Sp)
+{
+    Server &S = *Sp;
+    cudaSetDevice(S.h->device);
+    const size_t budget = S.h->budget;
+    for (;;) {
+        // retire finished batches
+        for (Slot &sl : S.slots)
+            if (sl.busy && cudaEventQuery(sl.done) == cudaSuccess)
+                complete_slot(S, sl);
+        std::unique_lock<std::mutex> lk(S.mu);
+        if (S.stop && S.pending.empty() && S.inflight == 0)
+            break;
+        Slot *free_slot = nullptr;
+        for (Slot &sl : S.slots)
+            if (!sl.busy) {
+                free_slot = &sl;
+                break;
+            }
+        std::vector<Request> batch;
+        if (free_slot && !S.pending.empty())
+            batch = take_batch(S, budget);
+        if (batch.empty()) {
+            S.cv.notify_all();
+            // nothing to launch: wait for a submit or poll the busy slots soon
+            S.cv.wait_for(lk, std::chrono::microseconds(S.inflight ? 20 : 2000));
+            continue;
+        }
+        size_t bytes = 0;
+        for (const Request &r : batch)
+            bytes += request_bytes((uint32_t)r.n, (uint32_t)r.m);
+        S.in_use += bytes + 4096;
+        S.inflight++;
+        free_slot->busy = true;
+        lk.unlock();
+        cudaError_t e = launch_batch(S, *free_slot, batch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            std::lock_guard<std::mutex> g(S.mu);
+            S.error = e;
+            for (const Request &r : batch) {
+                Outcome &o = S.results[r.ticket];
+                o.done = true;
+                o.status = e == cudaErrorMemoryAllocation ? MST_ERR_OOM : MST_ERR_CUDA;
+            }
+            S.in_use -= bytes + 4096;
+            S.inflight--;
+            free_slot->busy = false;
+            free_slot->tickets.clear();
+            if (free_slot->ws) {
+                cudaFreeAsync(free_slot->ws, free_slot->stream);
+                free_slot->ws = nullptr;
+            }
+        } else {
+            free_slot->ws_bytes = bytes + 4096;  // the admission charge
+        }
+    }
+}
+
+mst_status server_start(mst_handle h, int streams, int max_batch)
+{
+    if (h->server)
+        return MST_ERR_INVALID_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess)
+        return MST_ERR_CUDA;
+    Server *S = new Server();
+    S->h = h;
+    S->max_batch = max_batch;
+    S->slots.resize(streams);
+    for (Slot &sl : S->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            delete S;
+            return MST_ERR_CUDA;
+        }
+    }
+    h->server = S;
+    S->thr = std::thread(server_loop, S);
+    return MST_OK;
+}
+
+mst_status server_submit(mst_handle h, const Request &r, uint64_t *ticket)
+{
+    Server *S = h->server;
+    if (!S)
+        return MST_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop)
+        return MST_ERR_INVALID_ARG;
+    Request q = r;
+    q.ticket = S->next_ticket++;
+    S->submit_us[q.ticket] = q.t_submit_us;
+    S->results[q.ticket] = Outcome();
+    S->pending.push_back(q);
+    *ticket = q.ticket;
+    S->cv.notify_all();
+    return MST_OK;
+}
+
+mst_status server_poll(mst_handle h, uint64_t ticket, int *done, double *latency_us)
+{
+    Server *S = h->server;
+    if (!S)
+        return MST_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->results.find(ticket);
+    if (it == S->results.end())
+        return MST_ERR_INVALID_ARG;
+    *done = it->second.done ? 1 : 0;
+    if (!it->second.done)
+        return MST_OK;
+    if (latency_us)
+        *latency_us = it->second.latency_us;
+    const mst_status st = it->second.status;
+    S->results.erase(it);
+    return st;
+}
+
+mst_status server_drain(mst_handle h)
+{
+    Server *S = h->server;
+    if (!S)
+        return MST_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->cv.wait(lk, [&] { return S->pending.empty() && S->inflight == 0; });
+    return S->error == cudaSuccess ? MST_OK : MST_ERR_CUDA;
+}
+
+mst_status server_stop(mst_handle h)
+{
+    Server *S = h->server;
+    if (!S)
+        return MST_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv.notify_all();
+    }
+    S->thr.join();
+    cudaSetDevice(h->device);
+    for (Slot &sl : S->slots) {
+        if (sl.stream)
+            cudaStreamSynchronize(sl.stream);
+        if (sl.done)
+            cudaEventDestroy(sl.done);
+        if (sl.stream)
+            cudaStreamDestroy(sl.stream);
+        if (sl.h_desc)
+            cudaFreeHost(sl.h_desc);
+        if (sl.d_desc)
+            cudaFree(sl.d_desc);
+    }
+    const mst_status st = S->error == cudaSuccess ? MST_OK : MST_ERR_CUDA;
+    delete S;
+    h->server = nullptr;
+    return st;
+}
+
+}  // namespace mst

@@ -1,0 +1,110 @@
+"""Continuous-batching server: every request's tree equals the oracle's for
+that graph alone while other requests are queued and in flight; admission
+respects the memory budget."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from conftest import to_dev
+from paper_2005_06913_gb300 import binding as B
+from paper_2005_06913_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+def submit_all(h, graphs, gap_s=0.0):
+    reqs = []
+    for g in graphs:
+        s, d, w = to_dev(g.src, g.dst, g.w)
+        out = torch.full((max(g.n - 1, 1),), -5, dtype=torch.int32, device="cuda")
+        cnt = torch.full((1,), -5, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        wt = B.MST_W_F32 if g.w.dtype == np.float32 else B.MST_W_U32
+        st, t = B.mst_submit(h, wt, g.n, g.m, s, d, w, out, cnt)
+        assert st == B.MST_OK
+        reqs.append((t, g, out, cnt, (s, d, w)))
+        if gap_s:
+            time.sleep(gap_s)
+    return reqs
+
+
+def wait_all(h, reqs, timeout_s=120):
+    res = {}
+    t0 = time.time()
+    while len(res) < len(reqs):
+        assert time.time() - t0 < timeout_s, "server did not finish"
+        for t, *_ in reqs:
+            if t in res:
+                continue
+            st, done, lat = B.mst_poll(h, t)
+            if done:
+                res[t] = (st, lat)
+        time.sleep(0.001)
+    return res
+
+
+def test_serving_mix_matches_oracle(lib_built):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    pool = gg.serving_pool(60, 64, 30000, 6, 21)
+    graphs = [pool.graph(i) for i in range(pool.G)]
+    h = B.mst_create(0, 0)
+    try:
+        assert B.mst_server_start(h, 3, 16) == B.MST_OK
+        reqs = submit_all(h, graphs, gap_s=0.0005)
+        res = wait_all(h, reqs)
+        assert B.mst_server_drain(h) == B.MST_OK
+        for t, g, out, cnt, _ in reqs:
+            st, lat = res[t]
+            assert st == B.MST_OK and lat > 0
+            got = out[: int(cnt.item())].cpu().numpy().astype(np.int64)
+            assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w))
+        # alone == in the mix: a plain single solve of each graph gives the same ids
+        for t, g, out, cnt, (s, d, w) in reqs[:10]:
+            ids, _ = B.solve(h, g.n, s, d, w)
+            assert np.array_equal(ids.cpu().numpy(), out[: int(cnt.item())].cpu().numpy())
+    finally:
+        B.mst_server_stop(h)
+        B.mst_destroy(h)
+
+
+def test_serving_budget_admission(lib_built):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    small = [gg.random_connected(2000, 6000, i, weights="f32") for i in range(12)]
+    big = gg.random_connected(200000, 600000, 99, weights="f32")
+    h = B.mst_create(0, 8 << 20)  # 8 MiB: the big request can never be admitted
+    try:
+        assert B.mst_server_start(h, 2, 4) == B.MST_OK
+        reqs = submit_all(h, small[:6] + [big] + small[6:])
+        res = wait_all(h, reqs)
+        for t, g, out, cnt, _ in reqs:
+            st, _ = res[t]
+            if g is big:
+                assert st == B.MST_ERR_BUDGET
+            else:
+                assert st == B.MST_OK
+                got = out[: int(cnt.item())].cpu().numpy().astype(np.int64)
+                assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w))
+    finally:
+        B.mst_server_stop(h)
+        B.mst_destroy(h)
+
+
+def test_server_lifecycle_errors(lib_built):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    h = B.mst_create(0, 0)
+    try:
+        assert B.mst_submit(h, 0, 3, 0, None, None, None, None, 0)[0] != B.MST_OK
+        assert B.mst_server_start(h, 0, 4) == B.MST_ERR_INVALID_ARG
+        assert B.mst_server_start(h, 2, 4) == B.MST_OK
+        assert B.mst_server_start(h, 2, 4) == B.MST_ERR_INVALID_ARG
+        assert B.mst_poll(h, 12345)[0] == B.MST_ERR_INVALID_ARG
+        assert B.mst_server_stop(h) == B.MST_OK
+        assert B.mst_server_stop(h) == B.MST_ERR_INVALID_ARG
+    finally:
+        B.mst_destroy(h)

@@ -41,11 +41,29 @@ def check(h, n, src, dst, w):
     return got
 
 
+@pytest.fixture(params=[1, 2], ids=["fused", "graph"])
+def sched(request, handle):
+    """Runs a test under each single-graph schedule."""
+    assert B.mst_set_single_schedule(handle, request.param, 0) == B.MST_OK
+    yield handle
+    B.mst_set_single_schedule(handle, 0, 0)
+
+
 @pytest.mark.parametrize("n,m", [(2, 1), (3, 3), (17, 40), (1000, 3001), (1023, 1022),
                                  (1025, 4100), (4096, 32768), (5000, 200000), (70001, 250003)])
-def test_random_connected(handle, n, m):
+def test_random_connected(sched, n, m):
     g = gg.random_connected(n, m, n * 7 + m)
-    check(handle, g.n, g.src, g.dst, g.w)
+    check(sched, g.n, g.src, g.dst, g.w)
+
+
+@pytest.mark.parametrize("bps", [1, 2, 8])
+def test_fused_grid_sizes(handle, bps):
+    assert B.mst_set_single_schedule(handle, 1, bps) == B.MST_OK
+    try:
+        g = gg.random_connected(30000, 90001, 5 + bps)
+        check(handle, g.n, g.src, g.dst, g.w)
+    finally:
+        B.mst_set_single_schedule(handle, 0, 4)
 
 
 def test_config1(handle):
@@ -53,9 +71,9 @@ def test_config1(handle):
     check(handle, g.n, g.src, g.dst, g.w)
 
 
-def test_config2_grid_full(handle):
+def test_config2_grid_full(sched):
     g = gg.config(2)
-    check(handle, g.n, g.src, g.dst, g.w)
+    check(sched, g.n, g.src, g.dst, g.w)
 
 
 def test_grid_unshuffled(handle):
@@ -64,15 +82,15 @@ def test_grid_unshuffled(handle):
 
 
 @pytest.mark.parametrize("scale", [10, 14, 18])
-def test_rmat(handle, scale):
+def test_rmat(sched, scale):
     g = gg.rmat(scale, 8, 50 + scale)
-    check(handle, g.n, g.src, g.dst, g.w)
+    check(sched, g.n, g.src, g.dst, g.w)
 
 
 @pytest.mark.slow
-def test_config3_rmat_full(handle):
+def test_config3_rmat_full(sched):
     g = gg.config(3)
-    check(handle, g.n, g.src, g.dst, g.w)
+    check(sched, g.n, g.src, g.dst, g.w)
 
 
 @pytest.mark.parametrize("name", ["Graph10K_3", "Graph100K_6", "Graph1M_9"])
@@ -81,7 +99,8 @@ def test_paper_table1_shapes(handle, name):
     check(handle, g.n, g.src, g.dst, g.w)
 
 
-def test_float_weights_with_ties(handle):
+def test_float_weights_with_ties(sched):
+    handle = sched
     g = gg.random_connected(20000, 60000, 5, weights="f32")
     g.w[:] = np.round(g.w * 64) / 64  # force many ties
     g.w[::7] = np.float32(-0.0)
@@ -98,15 +117,15 @@ def test_u32_ties_and_multi_edges(handle):
     check(handle, n, src, dst, w)
 
 
-def test_increasing_path_deep_chain(handle):
+def test_increasing_path_deep_chain(sched):
     n = 300000  # every vertex hooks to its left neighbour: depth n-1 chain
     src = np.arange(n - 1, dtype=np.int32)
     dst = src + 1
     w = np.arange(1, n, dtype=np.uint32)
-    got = check(handle, n, src, dst, w)
+    got = check(sched, n, src, dst, w)
     assert len(got) == n - 1
     rev = (n - 1 - np.arange(n - 1)).astype(np.uint32)  # decreasing: chain the other way
-    check(handle, n, src, dst, rev)
+    check(sched, n, src, dst, rev)
 
 
 def test_star_and_cycle(handle):
@@ -130,7 +149,8 @@ def test_parallel_edges_only(handle):
     assert list(check(handle, 2, src, dst, w)) == [int(np.argmin(w))]
 
 
-def test_disconnected_and_isolated(handle):
+def test_disconnected_and_isolated(sched):
+    handle = sched
     a = gg.random_connected(4000, 9000, 1)
     b = gg.random_connected(3000, 7000, 2)
     src = np.concatenate([a.src, b.src + 4000]).astype(np.int32)
@@ -212,7 +232,8 @@ def test_workspace_reuse_and_growth(handle):
         check(handle, g.n, g.src, g.dst, g.w)
 
 
-def test_deterministic_rounds(handle):
+def test_deterministic_rounds(sched):
+    handle = sched
     g = gg.random_connected(50000, 200000, 11)
     ref = None
     for _ in range(10):
@@ -235,3 +256,28 @@ def test_async_on_side_stream(handle):
     with torch.cuda.stream(s):
         got, status = gpu_solve(handle, g.n, g.src, g.dst, g.w, stream=s)
     assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w))
+
+
+def test_host_buffer_solve(handle):
+    g = gg.random_connected(20000, 80000, 17)
+    hs, hd = torch.from_numpy(g.src), torch.from_numpy(g.dst)
+    hw = torch.from_numpy(g.w.view(np.int32))
+    ho = torch.full((g.n - 1,), -1, dtype=torch.int32)
+    hc = torch.zeros(1, dtype=torch.int64)
+    st = B.mst_solve_host(handle, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc)
+    assert st == B.MST_OK
+    assert np.array_equal(ho[: int(hc.item())].numpy(), oracle.kruskal(g.n, g.src, g.dst, g.w))
+
+
+def test_profile_replay_matches(handle):
+    g = gg.random_connected(50000, 200000, 23)
+    s, d, w = to_dev(g.src, g.dst, g.w)  # kept alive: the replay reuses these buffers
+    out = torch.full((g.n - 1,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert B.mst_solve(handle, g.n, g.m, s, d, w, out, cnt) == B.MST_OK
+    first = out.clone()
+    prof = B.mst_profile_last_solve(handle)
+    assert torch.equal(first, out)  # the replay writes the same tree again
+    names = [p["name"] for p in prof]
+    assert "k_find0" in names and "k_compact<R0>" in names and "k_emit" in names
+    assert all(p["total_ms"] > 0 and p["launches"] >= 1 for p in prof)

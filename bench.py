@@ -45,6 +45,26 @@ def workload(cfg: int):
     return g, names[cfg]
 
 
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/ncu_traffic.txt: "kernel source_sha256 bytes_per_launch"),
+    or None when absent or taken on different kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = os.path.join(ROOT, "paper_2005_06913_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        h.update(open(os.path.join(src, f), "rb").read())
+    sha = h.hexdigest()[:16]
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == sha:
+            return float(f[2])
+    return None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -237,6 +257,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     h = B.mst_create(dev, 0)
+    B.mst_set_single_schedule(h, 1 if args.schedule == "fused" else 2, 0)
 
     def solve():
         st = B.mst_solve(h, g.n, g.m, src, dst, w, out, cnt, stream)
@@ -281,23 +302,30 @@ def run_ours(args):
     clocks = clk.summary()
     rounds_e, rounds_v = B.mst_get_round_stats(h, stream)
 
-    # per-kernel CUDA-event replay of the same solve: dominant kernel + bytes
+    # per-phase times of the timed kernel (fused schedule: its own phase log)
     prof = B.mst_profile_last_solve(h, stream)
-    launches_per_step = sum(p["launches"] for p in prof)
-    dom = max(prof, key=lambda p: p["total_ms"])
     hbm_peak, peak_kind = peaks()
-    achieved = dom["alg_bytes"] / (dom["total_ms"] * 1e-3) / 1e9
     solve_bytes = sum(p["alg_bytes"] for p in prof)
-    kernels = [{"name": p["name"], "launches": p["launches"], "ms": round(p["total_ms"], 4),
+    step_s = total_ms / args.steps * 1e-3
+    kernels = [{"name": p["name"], "count": p["launches"], "ms": round(p["total_ms"], 4),
                 "alg_MB": round(p["alg_bytes"] / 1e6, 3),
-                "GBps": round(p["alg_bytes"] / (p["total_ms"] * 1e-3) / 1e9, 1)} for p in prof]
-    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "launches_per_step": dom["launches"],
-                "share_of_replay": dom["total_ms"] / sum(p["total_ms"] for p in prof),
-                "solve_alg_bytes": solve_bytes,
-                "solve_frac": solve_bytes / (total_ms / args.steps * 1e-3) / 1e9 / hbm_peak}
+                "GBps": round(p["alg_bytes"] / max(p["total_ms"], 1e-9) / 1e6, 1)} for p in prof]
+    if args.schedule == "fused":
+        launches_per_step = 1
+        dom_name, dom_bytes, dom_s, dom_launches = "k_solve", solve_bytes, step_s, 1
+    else:
+        launches_per_step = sum(p["launches"] for p in prof)
+        dom = max(prof, key=lambda p: p["total_ms"])
+        dom_name, dom_bytes, dom_s, dom_launches = (dom["name"], dom["alg_bytes"],
+                                                    dom["total_ms"] * 1e-3, dom["launches"])
+    achieved = dom_bytes / dom_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_for(dom_name),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",
+                "launches_per_step": dom_launches,
+                "alg_bytes_per_launch": dom_bytes / max(dom_launches, 1),
+                "duration_source": "CUDA events per step (whole solve)" if args.schedule == "fused"
+                else "CUDA-event replay of each kernel"}
 
     # end to end through the host-buffer C-ABI call, copies inside the timed region
     e2e = None
@@ -315,7 +343,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "timer": "CUDA events per step on the launching stream"},
         "roofline": roofline,
-        "kernel_replay": kernels,
+        "phases" if args.schedule == "fused" else "kernel_replay": kernels,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -342,6 +370,7 @@ def main():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--schedule", choices=["fused", "graph"], default="fused")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

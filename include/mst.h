@@ -158,13 +158,17 @@ typedef struct {
 } mst_kernel_profile;
 
 /*
- * Re-runs the handle's last single-graph solve (same device buffers, which
- * must still be valid) launching each kernel separately between two CUDA
- * events on `stream`, and reports per kernel the launch count, the summed
- * event time and the bytes the method must move through DRAM in those
- * launches (edge lists and per-vertex arrays; label gathers and atomics,
- * which stay in L2, are not counted).  Writes at most `cap` entries and sets
- * *count.  Synchronises `stream`; the outputs are written again.
+ * Per-kernel (or per-phase) time and traffic model of the handle's last
+ * single-graph solve.  Under the fused schedule (the default) the entries
+ * are the phases of the one cooperative kernel (init, find0, hook,
+ * compress, compact, emit), timed inside that kernel itself by %globaltimer
+ * stamps at each grid barrier; nothing is re-run.  Under the graph schedule
+ * the solve is re-run (same device buffers, which must still be valid) with
+ * each kernel launched separately between two CUDA events on `stream`, and
+ * the outputs are written again.  alg_bytes counts the bytes the method must
+ * move through DRAM (edge lists and per-vertex arrays; label gathers and
+ * atomics, which stay in L2, are not counted).  Writes at most `cap`
+ * entries, sets *count, and synchronises `stream`.
  */
 mst_status mst_profile_last_solve(mst_handle h, void *stream, mst_kernel_profile *out,
                                   int32_t cap, int32_t *count);

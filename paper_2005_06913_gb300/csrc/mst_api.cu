@@ -221,8 +221,10 @@ mst_status mst_profile_last_solve(mst_handle h, void *stream, mst_kernel_profile
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return MST_ERR_CUDA;
-    cudaError_t e = single_profile(h->single, L.src, L.dst, L.w, L.wt, L.out, L.out_count, L.n,
-                                   L.m, s, prof);
+    cudaError_t e = h->single.schedule == 2
+                        ? single_profile(h->single, L.src, L.dst, L.w, L.wt, L.out, L.out_count,
+                                         L.n, L.m, s, prof)
+                        : single_phase_profile(h->single, s, prof);
     if (e != cudaSuccess)
         return cuda_status(e);
     int32_t k = 0;

@@ -264,6 +264,15 @@ struct GraphArrays {
     uint32_t *bits;
 };
 
+// Offers a key to a running minimum that may live in shared or global
+// memory (generic pointer): a filtered atomicMin (values only decrease, so a
+// key not below the current value cannot win).
+__device__ __forceinline__ void offer_any(unsigned long long *p, unsigned long long key)
+{
+    if (key < *(volatile unsigned long long *)p)
+        atomicMin(p, key);
+}
+
 // Pointer chase with path halving through a volatile view (the array may
 // live in shared or global memory; one team owns it).
 __device__ __forceinline__ bool chase_v(volatile int32_t *parent, uint32_t start, uint32_t &at)
@@ -315,8 +324,8 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
         if (u == v)
             continue;
         const unsigned long long key = make_key(weight_bits(__ldg(w + e), wt, status), e);
-        atomicMin(&A.mA[u], key);
-        atomicMin(&A.mA[v], key);
+        offer_any(&A.mA[u], key);
+        offer_any(&A.mA[v], key);
     }
     tm.sync();
     uint32_t n_r = n, m_r = m;
@@ -445,8 +454,8 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
                     const uint32_t pos = run + rank[j];
                     A.E[pos] = rec[j];
                     const unsigned long long key = make_key(rec[j].z, pos);
-                    atomicMin(&mx[rec[j].x], key);
-                    atomicMin(&mx[rec[j].y], key);
+                    offer_any(&mx[rec[j].x], key);
+                    offer_any(&mx[rec[j].y], key);
                 }
             }
             run += total;

@@ -27,6 +27,17 @@ constexpr uint64_t kNoEdge = ~0ull;           // minimum[] = -1 of Section 2.1
 constexpr int kChaseLimit = 64;               // pointer hops per thread per pass
 constexpr uint32_t kMaxJumpPasses = 64;       // > log2(2^31): pointer jumping ends sooner
 constexpr uint32_t kSpinLimit = 1u << 22;     // iterations of any device wait
+constexpr int kMaxPhaseLog = 256;             // phase-log entries kept per fused solve
+
+// Phase kinds of the fused solve's phase log.
+enum : uint8_t { PH_START = 0, PH_INIT, PH_FIND0, PH_HOOK, PH_COMPRESS, PH_COMPACT, PH_EMIT };
+
+__device__ __forceinline__ unsigned long long global_timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Device status bits (mapped to mst_status on the host).
 enum : uint32_t {
@@ -62,6 +73,11 @@ struct Ctl {
     uint32_t flag3[3];   // per-pass "chase unfinished" flags of the fused kernel
     uint32_t emitted;    // tree edges written by emit (own field: m_next may still be read)
     uint32_t status;  // ST_* bits
+    uint32_t nphase;  // entries used in the phase log (fused schedule)
+    uint8_t phase_kind[kMaxPhaseLog];
+    uint8_t phase_round[kMaxPhaseLog];
+    unsigned long long phase_ns[kMaxPhaseLog];  // %globaltimer at each phase end
+    unsigned long long work_ns[kMaxPhaseLog];   // when CTA 0 finished its own work
     uint32_t stat_m[kMaxRounds + 1];
     uint32_t stat_n[kMaxRounds + 1];
 };
@@ -117,6 +133,53 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Fire-and-forget reductions (no returned value, so the issuing warp never
+// waits on them).
+__device__ __forceinline__ void red_min_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_or_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Offers `key` to the running minimum at p.  The load first filters keys
+// that cannot win: values at p only decrease, so a cached (possibly older)
+// value is never below the true one, and skipping key >= cached is exact.
+// On hot components this turns most same-address atomics into cache hits.
+__device__ __forceinline__ void offer_min(unsigned long long *p, unsigned long long key)
+{
+    if (key < __ldca(p))
+        red_min_u64(p, key);
+}
+
+// Whether offers go through the filtering load: measured on GB300, a plain
+// red.min.u64 sustains ~157 G/s on distinct addresses but ~1.5 G/s on one
+// hot address, while the filtered offer costs ~15-65% on distinct addresses
+// and is 25x faster on a hot one.  Filter when a target receives many
+// offers on average (hot spots likely): at least 8 per target.
+__device__ __forceinline__ bool use_filter(uint32_t m_cur, uint32_t targets)
+{
+    return 2ull * m_cur >= 8ull * (unsigned long long)(targets > 0 ? targets : 1);
+}
+
+// Warp-cooperative offer: lanes in `active` (all calling) offer keys to
+// components c; lanes naming the same component first agree on their
+// minimum (64-bit key as high word, then low word), and one lane per
+// distinct component offers it.
+__device__ __forceinline__ void offer_min_grouped(unsigned long long *arr, uint32_t active,
+                                                  uint32_t c, unsigned long long key)
+{
+    const uint32_t grp = __match_any_sync(active, c);
+    const uint32_t hi = __reduce_min_sync(grp, (uint32_t)(key >> 32));
+    const uint32_t lo = __reduce_min_sync(grp, (uint32_t)(key >> 32) == hi ? (uint32_t)key
+                                                                           : 0xffffffffu);
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1))
+        offer_min(arr + c, ((unsigned long long)hi << 32) | lo);
 }
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p)

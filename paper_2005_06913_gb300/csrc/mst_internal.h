@@ -14,7 +14,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/mst.h"
+#include "mst.h"
 #include "mst_common.cuh"
 
 namespace mst {
@@ -53,6 +53,8 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n,
                           uint32_t m, cudaStream_t stream);
 double single_alg_bytes(const Ctl &c);
+// Per-phase times of the last fused solve (its own phase log; synchronous).
+cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<KernelProfile> &prof);
 // Replays a solve kernel by kernel between CUDA events (synchronous).
 cudaError_t single_profile(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                            uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n, uint32_t m,

@@ -92,6 +92,7 @@ __device__ __forceinline__ void find0_range(const Ws &ws, const int32_t *src, co
 {
     unsigned long long *mn = ws.mins[0];
     const size_t groups = ((size_t)m + 3) >> 2;
+    const bool filtered = use_filter(m, n);
     for (size_t g = g0; g < groups; g += gstep) {
         const uint32_t e0 = (uint32_t)(g << 2);
         int32_t us[4], vs[4];
@@ -109,79 +110,109 @@ __device__ __forceinline__ void find0_range(const Ws &ws, const int32_t *src, co
             if (u == v)
                 continue;
             const unsigned long long key = make_key(weight_bits(wr[j], wt, status), e0 + j);
-            atomicMin(&mn[u], key);
-            atomicMin(&mn[v], key);
+            if (filtered) {
+                offer_min(&mn[u], key);
+                offer_min(&mn[v], key);
+            } else {
+                red_min_u64(&mn[u], key);
+                red_min_u64(&mn[v], key);
+            }
         }
     }
 }
 
-// Hook one tile of components (Section 2.1 steps 30-40) and give the tile's
-// roots dense new ids.  The block owning the last tile stores n_next.
+// Warp tiles: one warp owns a tile of kHookIpl*32 components or kCompIpl*32
+// edges (item j of lane l is tile index j*32 + l, so every load of the warp
+// is contiguous), ranks its items with ballots, takes its offset from the
+// decoupled look-back and writes its results itself.  No block barrier is
+// involved, so a warp waiting on memory or on its predecessor never holds
+// up the other warps of its CTA.
+constexpr int kHookIpl = 4, kCompIpl = 8;
+// Below this many components, compaction would combine a warp's offers per
+// component (match + reduce) before touching memory.  Measured on GB300 it
+// costs more than it saves on both the grid and the R-MAT workloads (the
+// filtered offer already removes the hot-spot atomics), so it is off.
+constexpr uint32_t kGroupedMaxComponents = 0u;  // measured: grouping costs more than it saves
+
+constexpr int kHookWTile = 32 * kHookIpl, kCompWTile = 32 * kCompIpl;
+
+// Hook one warp tile of components (Section 2.1 steps 30-40) and give the
+// tile's roots dense new ids.  The warp owning the last tile stores n_next.
 template <bool R0>
-__device__ __forceinline__ void hook_tile(const Ws &ws, Ctl *c, uint32_t tile, uint32_t ntiles,
-                                          uint32_t round, uint32_t epoch, uint32_t n_cur,
-                                          const int32_t *src, const int32_t *dst, TileSmem &sm)
+__device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, uint32_t ntiles,
+                                           uint32_t round, uint32_t epoch, uint32_t n_cur,
+                                           const int32_t *src, const int32_t *dst)
 {
+    const int lane = threadIdx.x & 31;
     const unsigned long long *mcur = (round & 1) ? ws.mins[1] : ws.mins[0];
     unsigned long long *mnext = (round & 1) ? ws.mins[0] : ws.mins[1];
     const uint4 *ecur = (round & 1) ? ws.E[1] : ws.E[0];
     int32_t *parent = ws.parent;
-    const uint32_t base = tile * kTile;
-    bool root[kItems];
-    uint32_t vv[kItems];
+    const uint32_t base = tile * kHookWTile;
+    unsigned long long k[kHookIpl];
 #pragma unroll
-    for (int j = 0; j < kItems; j++) {
-        const uint32_t v = base + j * kThreads + threadIdx.x;
-        vv[j] = v;
-        root[j] = false;
-        if (v < n_cur) {
-            const unsigned long long k = mcur[v];
+    for (int j = 0; j < kHookIpl; j++) {
+        const uint32_t v = base + j * 32 + lane;
+        k[j] = v < n_cur ? mcur[v] : kNoEdge;
+    }
+    uint32_t a[kHookIpl], b[kHookIpl], id[kHookIpl];
+#pragma unroll
+    for (int j = 0; j < kHookIpl; j++) {
+        const uint32_t v = base + j * 32 + lane;
+        if (v < n_cur)
             mnext[v] = kNoEdge;
-            if (k == kNoEdge) {
-                root[j] = true;  // no edge leaves this component
+        a[j] = b[j] = id[j] = 0;
+        if (k[j] != kNoEdge) {
+            const uint32_t p = (uint32_t)k[j];
+            if (R0) {
+                a[j] = (uint32_t)__ldg(src + p);
+                b[j] = (uint32_t)__ldg(dst + p);
+                id[j] = p;
             } else {
-                const uint32_t p = (uint32_t)k;
-                uint32_t a, b, id;
-                if (R0) {
-                    a = (uint32_t)__ldg(src + p);
-                    b = (uint32_t)__ldg(dst + p);
-                    id = p;
-                } else {
-                    const uint4 r = ecur[p];
-                    a = r.x;
-                    b = r.y;
-                    id = r.w;
-                }
-                const uint32_t d = (a == v) ? b : a;
-                const unsigned long long kd = mcur[d];
-                if ((uint32_t)kd == p && v < d) {
-                    root[j] = true;  // mutual choice: the lower id stays root
-                } else {
-                    parent[v] = (int32_t)d;
-                    atomicOr(&ws.mst_bits[id >> 5], 1u << (id & 31));
-                }
+                const uint4 r = ecur[p];
+                a[j] = r.x;
+                b[j] = r.y;
+                id[j] = r.w;
             }
-            if (root[j])
-                parent[v] = (int32_t)v;
         }
     }
-    uint32_t rank[kItems], total;
-    tile_ranks_striped(root, rank, total, sm.s32);
-    if (threadIdx.x < 32) {
-        const uint32_t ex = lookback_warp(ws.desc, tile, total, epoch, &c->status);
-        if (threadIdx.x == 0) {
-            sm.s_excl = ex;
-            if (tile == ntiles - 1)
-                c->n_next = ex + total;
-        }
-    }
-    __syncthreads();
-    const uint32_t ex = sm.s_excl;
+    unsigned long long kd[kHookIpl];
 #pragma unroll
-    for (int j = 0; j < kItems; j++)
-        if (root[j])
-            ws.nid[vv[j]] = (int32_t)(ex + rank[j]);
-    __syncthreads();  // s32/s_excl free for the next tile
+    for (int j = 0; j < kHookIpl; j++) {
+        const uint32_t v = base + j * 32 + lane;
+        const uint32_t d = (a[j] == v) ? b[j] : a[j];
+        a[j] = d;  // a now holds the other component
+        kd[j] = k[j] != kNoEdge ? mcur[d] : kNoEdge;
+    }
+    uint32_t mask[kHookIpl], total = 0;
+#pragma unroll
+    for (int j = 0; j < kHookIpl; j++) {
+        const uint32_t v = base + j * 32 + lane;
+        bool root = false;
+        if (v < n_cur) {
+            const uint32_t d = a[j];
+            if (k[j] == kNoEdge || ((uint32_t)kd[j] == (uint32_t)k[j] && v < d)) {
+                root = true;  // no edge leaves it, or the lower id of a mutual pair
+                parent[v] = (int32_t)v;
+            } else {
+                parent[v] = (int32_t)d;
+                red_or_u32(&ws.mst_bits[id[j] >> 5], 1u << (id[j] & 31));
+            }
+        }
+        mask[j] = __ballot_sync(0xffffffffu, root);
+        total += __popc(mask[j]);
+    }
+    const uint32_t ex = lookback_warp(ws.desc, tile, total, epoch, &c->status);
+    if (lane == 0 && tile == ntiles - 1)
+        c->n_next = ex + total;
+    const uint32_t lt = lanemask_lt();
+    uint32_t run = ex;
+#pragma unroll
+    for (int j = 0; j < kHookIpl; j++) {
+        if ((mask[j] >> lane) & 1u)
+            ws.nid[base + j * 32 + lane] = (int32_t)(run + __popc(mask[j] & lt));
+        run += __popc(mask[j]);
+    }
 }
 
 // Follows hook pointers from `start` with path halving, at most kChaseLimit
@@ -236,87 +267,88 @@ __device__ __forceinline__ bool compress_range(const Ws &ws, uint32_t n_cur, boo
     return unfinished;
 }
 
-// Compaction of one tile of round r's live edges fused with find-min of
-// round r+1.  The block owning the last tile stores m_next.
+// Compaction of one warp tile of round r's live edges fused with find-min
+// of round r+1: survivors are written from registers to consecutive
+// positions (one contiguous run per row of the tile) and offer their keys
+// with fire-and-forget reductions.  The warp owning the last tile stores
+// m_next.
 template <bool R0>
-__device__ __forceinline__ void compact_tile(const Ws &ws, Ctl *c, uint32_t tile, uint32_t ntiles,
-                                             uint32_t round, uint32_t epoch, uint32_t m_cur,
-                                             uint32_t n_next, uint32_t n_in, uint32_t wt,
-                                             uint32_t vec, const int32_t *src, const int32_t *dst,
-                                             const uint32_t *w, TileSmem &sm)
+__device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t tile,
+                                              uint32_t ntiles, uint32_t round, uint32_t epoch,
+                                              uint32_t m_cur, uint32_t n_next, uint32_t n_in,
+                                              uint32_t wt, const int32_t *src, const int32_t *dst,
+                                              const uint32_t *w)
 {
+    const int lane = threadIdx.x & 31;
     const uint4 *ecur = (round & 1) ? ws.E[1] : ws.E[0];
     uint4 *enext = (round & 1) ? ws.E[0] : ws.E[1];
     unsigned long long *mnext = (round & 1) ? ws.mins[0] : ws.mins[1];
     const int32_t *__restrict__ lab = ws.lab;
     uint32_t *status = &c->status;
-    const uint32_t base = tile * kTile;
-    bool keep[kItems];
-    uint4 rec[kItems];
-    uint32_t rank[kItems], total;
-    if (R0) {
-        const uint32_t e0 = base + threadIdx.x * kItems;
-        int32_t us[4], vs[4];
-        uint32_t wr[4];
-        load4_soa(src, dst, w, e0, m_cur, vec, us, vs, wr);
+    const uint32_t base = tile * kCompWTile;
+    uint4 rec[kCompIpl];
+    bool ok[kCompIpl];
 #pragma unroll
-        for (int j = 0; j < kItems; j++) {
-            keep[j] = false;
-            rec[j] = make_uint4(0, 0, 0, 0);
-            const uint32_t u = (uint32_t)us[j], v = (uint32_t)vs[j];
-            if (e0 + j < m_cur && u < n_in && v < n_in && u != v) {
-                const uint32_t nu = (uint32_t)lab[u], nv = (uint32_t)lab[v];
-                if (nu >= n_next || nv >= n_next) {
-                    atomicOr(status, ST_INTERNAL);  // never for a valid forest
-                } else if (nu != nv) {
-                    keep[j] = true;
-                    rec[j] = make_uint4(nu, nv, weight_bits(wr[j], wt, status), e0 + j);
-                }
+    for (int j = 0; j < kCompIpl; j++) {
+        const uint32_t i = base + j * 32 + lane;
+        const bool in = i < m_cur;
+        if (R0) {
+            const uint32_t u = in ? (uint32_t)__ldg(src + i) : 0u;
+            const uint32_t v = in ? (uint32_t)__ldg(dst + i) : 0u;
+            const uint32_t x = in ? __ldg(w + i) : 0u;
+            ok[j] = in && u < n_in && v < n_in && u != v;
+            rec[j] = make_uint4(u, v, x, i);
+        } else {
+            rec[j] = in ? ecur[i] : make_uint4(0, 0, 0, 0);
+            ok[j] = in;
+        }
+    }
+    uint32_t mask[kCompIpl], total = 0;
+#pragma unroll
+    for (int j = 0; j < kCompIpl; j++) {
+        bool keep = false;
+        if (ok[j]) {
+            const uint32_t nu = (uint32_t)lab[rec[j].x], nv = (uint32_t)lab[rec[j].y];
+            if (nu >= n_next || nv >= n_next) {
+                atomicOr(status, ST_INTERNAL);  // never for a valid forest
+            } else if (nu != nv) {
+                keep = true;
+                rec[j].x = nu;
+                rec[j].y = nv;
+                if (R0)
+                    rec[j].z = weight_bits(rec[j].z, wt, status);
             }
         }
-        tile_ranks_blocked(keep, rank, total, sm.s32);
-    } else {
+        mask[j] = __ballot_sync(0xffffffffu, keep);
+        total += __popc(mask[j]);
+    }
+    const uint32_t ex = lookback_warp(ws.desc, tile, total, epoch, status);
+    if (lane == 0 && tile == ntiles - 1)
+        c->m_next = ex + total;
+    const uint32_t lt = lanemask_lt();
+    // few components left: many lanes of a warp offer to the same one
+    const bool grouped = n_next <= kGroupedMaxComponents;
+    const bool filtered = use_filter(m_cur, n_next);
+    uint32_t run = ex;
 #pragma unroll
-        for (int j = 0; j < kItems; j++) {
-            const uint32_t i = base + j * kThreads + threadIdx.x;
-            keep[j] = false;
-            rec[j] = make_uint4(0, 0, 0, 0);
-            if (i < m_cur) {
-                const uint4 r = ecur[i];
-                const uint32_t nu = (uint32_t)lab[r.x], nv = (uint32_t)lab[r.y];
-                if (nu >= n_next || nv >= n_next) {
-                    atomicOr(status, ST_INTERNAL);  // never for a valid forest
-                } else if (nu != nv) {
-                    keep[j] = true;
-                    rec[j] = make_uint4(nu, nv, r.z, r.w);
-                }
+    for (int j = 0; j < kCompIpl; j++) {
+        if ((mask[j] >> lane) & 1u) {
+            const uint32_t pos = run + __popc(mask[j] & lt);
+            enext[pos] = rec[j];
+            const unsigned long long key = make_key(rec[j].z, pos);
+            if (grouped) {
+                offer_min_grouped(mnext, mask[j], rec[j].x, key);
+                offer_min_grouped(mnext, mask[j], rec[j].y, key);
+            } else if (filtered) {
+                offer_min(&mnext[rec[j].x], key);
+                offer_min(&mnext[rec[j].y], key);
+            } else {
+                red_min_u64(&mnext[rec[j].x], key);
+                red_min_u64(&mnext[rec[j].y], key);
             }
         }
-        tile_ranks_striped(keep, rank, total, sm.s32);
+        run += __popc(mask[j]);
     }
-    if (threadIdx.x < 32) {
-        const uint32_t ex = lookback_warp(ws.desc, tile, total, epoch, status);
-        if (threadIdx.x == 0) {
-            sm.s_excl = ex;
-            if (tile == ntiles - 1)
-                c->m_next = ex + total;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < kItems; j++)
-        if (keep[j])
-            sm.stage[rank[j]] = rec[j];
-    __syncthreads();
-    const uint32_t ex = sm.s_excl;
-    for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
-        const uint4 r = sm.stage[i];
-        const uint32_t pos = ex + i;
-        enext[pos] = r;
-        const unsigned long long key = make_key(r.z, pos);
-        atomicMin(&mnext[r.x], key);
-        atomicMin(&mnext[r.y], key);
-    }
-    __syncthreads();  // stage/s32 free for the next tile
 }
 
 // Emits the tree edges of one tile of kEmitWords bit words, ascending: ids
@@ -397,45 +429,36 @@ __device__ __forceinline__ void finish(Ctl *c, int64_t *out_count, uint32_t emit
 
 // ----------------------------------------------------- grid-wide barrier
 
-// Two-level barrier for a co-resident (cooperative) grid: blocks arrive in
-// groups of 16 on separate counters; the last of each group arrives at the
-// top counter; the last group flips the generation word.  Waits are bounded:
-// on expiry ST_TIMEOUT is set and later barriers no longer wait.
-constexpr uint32_t kBarTop = 0, kBarGen = 32, kBarGroups = 64;
-constexpr uint32_t kBarSpinLimit = 1u << 21;
+// Grid barrier for a co-resident (cooperative) grid.  One counter: block 0
+// adds 2^31 - (grid - 1) and every other block adds 1, so the counter's top
+// bit flips exactly when the last block arrives and its low bits return to
+// where they were; each block spins until the top bit differs from the
+// value it saw when it arrived.  One atomic per block, nothing to reset.
+// Waits are bounded: on expiry ST_TIMEOUT is set and later barriers no
+// longer wait.
+constexpr uint32_t kBarCount = 0, kBarGen = 32;  // kBarGen: unused slot kept for layout
+constexpr uint32_t kBarSpinLimit = 1u << 22;
 
 __device__ __forceinline__ void grid_sync(uint32_t *bar, uint32_t &gen, uint32_t *status)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t g = gen;
         const uint32_t nb = gridDim.x;
-        const uint32_t grp = blockIdx.x >> 4;
-        const uint32_t ngrp = (nb + 15) >> 4;
-        const uint32_t gsize = min(16u, nb - (grp << 4));
-        uint32_t *gc = bar + kBarGroups + 32 * grp;
+        const uint32_t inc = blockIdx.x == 0 ? 0x80000000u - (nb - 1) : 1u;
         __threadfence();
-        if (atomicAdd(gc, 1u) == gsize - 1) {
-            atomicExch(gc, 0u);
-            __threadfence();
-            if (atomicAdd(bar + kBarTop, 1u) == ngrp - 1) {
-                atomicExch(bar + kBarTop, 0u);
-                __threadfence();
-                atomicExch(bar + kBarGen, g + 1);
-            }
-        }
+        const uint32_t old = atomicAdd(bar + kBarCount, inc);
         uint32_t spins = 0;
-        while (ld_volatile_u32(bar + kBarGen) == g) {
-            if (ld_volatile_u32(status) & ST_TIMEOUT)
-                break;
+        while (((old ^ ld_volatile_u32(bar + kBarCount)) & 0x80000000u) == 0) {
             if (++spins > kBarSpinLimit) {
                 atomicOr(status, ST_TIMEOUT);
-                printf("mst: grid barrier gave up: block %u of %u, generation %u, top %u, "
-                       "group %u count %u\n", blockIdx.x, nb, g, ld_volatile_u32(bar + kBarTop),
-                       grp, ld_volatile_u32(gc));
+                printf("mst: grid barrier gave up: block %u of %u, arrival value %u, now %u\n",
+                       blockIdx.x, nb, old, ld_volatile_u32(bar + kBarCount));
                 break;
             }
-            __nanosleep(32);
+            if (ld_volatile_u32(status) & ST_TIMEOUT)
+                break;
+            if (spins > 64)
+                __nanosleep(32);
         }
         __threadfence();
     }
@@ -443,14 +466,39 @@ __device__ __forceinline__ void grid_sync(uint32_t *bar, uint32_t &gen, uint32_t
     gen++;
 }
 
-size_t bar_words(int max_blocks) { return kBarGroups + 32 * (size_t)((max_blocks + 15) / 16); }
+size_t bar_words(int) { return 64; }
+
+// CTA 0 stamps when its own work of a phase is done (before the barrier)
+// and when the phase ends (everyone has passed the barrier).
+__device__ __forceinline__ void mark_work(Ctl *c)
+{
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t i = c->nphase;
+        if (i < (uint32_t)kMaxPhaseLog)
+            c->work_ns[i] = global_timer_ns();
+    }
+}
+
+__device__ __forceinline__ void log_phase(Ctl *c, uint8_t kind, uint32_t round = 0)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t i = c->nphase;
+        if (i < (uint32_t)kMaxPhaseLog) {
+            c->phase_kind[i] = kind;
+            c->phase_round[i] = (uint8_t)(round < 255 ? round : 255);
+            c->phase_ns[i] = global_timer_ns();
+            c->nphase = i + 1;
+        }
+    }
+}
 
 // ------------------------------------------------- fused persistent kernel
 
 // The whole solve in one cooperative launch.  Tiles are assigned statically
 // (tile t to block t mod grid, in increasing order), so every look-back wait
 // is on a tile whose block is resident and makes progress.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_t *out,
         int64_t *out_count, uint32_t n, uint32_t m, uint32_t wt, uint32_t vec)
 {
@@ -459,9 +507,12 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
     uint32_t *status = &c->status;
     const uint32_t nb = gridDim.x, bid = blockIdx.x;
     const size_t gtid = (size_t)bid * kThreads + threadIdx.x, gstride = (size_t)nb * kThreads;
-    uint32_t gen = ld_volatile_u32(ws.bar + kBarGen);
+    const uint32_t gw = bid * kWarps + (threadIdx.x >> 5), nw = nb * kWarps;  // global warp
+    uint32_t gen = 0;  // barrier count (the barrier itself keeps no generation)
     uint32_t ep = c->epoch;
+    log_phase(c, PH_START);
     init_range(ws, n, m, gtid, gstride);
+    mark_work(c);
     if (gtid == 0) {
         c->n = n;
         c->m = m;
@@ -474,22 +525,27 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         c->stat_n[0] = n;
     }
     grid_sync(ws.bar, gen, status);
+    log_phase(c, PH_INIT);
     find0_range(ws, src, dst, w, n, m, wt, vec, status, gtid, gstride);
+    mark_work(c);
     grid_sync(ws.bar, gen, status);
+    log_phase(c, PH_FIND0);
     uint32_t n_cur = n, m_cur = m, r = 0;
     for (;; r++) {
         // hook + new ids of the roots
-        const uint32_t nth = (n_cur + kTile - 1) / kTile;
+        const uint32_t nth = (n_cur + kHookWTile - 1) / kHookWTile;
         if (bid == 0 && threadIdx.x == 0)
             c->flag3[0] = 0;
-        for (uint32_t t = bid; t < nth; t += nb) {
+        for (uint32_t t = gw; t < nth; t += nw) {
             if (r == 0)
-                hook_tile<true>(ws, c, t, nth, r, ep, n_cur, src, dst, sm);
+                hook_wtile<true>(ws, c, t, nth, r, ep, n_cur, src, dst);
             else
-                hook_tile<false>(ws, c, t, nth, r, ep, n_cur, src, dst, sm);
+                hook_wtile<false>(ws, c, t, nth, r, ep, n_cur, src, dst);
         }
         ep++;
+        mark_work(c);
         grid_sync(ws.bar, gen, status);
+        log_phase(c, PH_HOOK, r);
         const uint32_t n_next = nth ? ld_volatile_u32(&c->n_next) : 0u;
         // compress, with extra pointer-jumping passes while chains are deep
         for (uint32_t pass = 0;; pass++) {
@@ -498,7 +554,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             const bool unf = compress_range(ws, n_cur, pass == 0, gtid, gstride);
             if (__syncthreads_or(unf ? 1 : 0) && threadIdx.x == 0)
                 c->flag3[pass % 3] = 1u;
+            mark_work(c);
             grid_sync(ws.bar, gen, status);
+            log_phase(c, PH_COMPRESS, r);
             if (!ld_volatile_u32(&c->flag3[pass % 3]))
                 break;
             if (pass + 1 >= kMaxJumpPasses) {
@@ -508,16 +566,17 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             }
         }
         // compact (+ find-min of the next round)
-        const uint32_t ntc = (m_cur + kTile - 1) / kTile;
-        for (uint32_t t = bid; t < ntc; t += nb) {
+        const uint32_t ntc = (m_cur + kCompWTile - 1) / kCompWTile;
+        for (uint32_t t = gw; t < ntc; t += nw) {
             if (r == 0)
-                compact_tile<true>(ws, c, t, ntc, r, ep, m_cur, n_next, n, wt, vec, src, dst, w, sm);
+                compact_wtile<true>(ws, c, t, ntc, r, ep, m_cur, n_next, n, wt, src, dst, w);
             else
-                compact_tile<false>(ws, c, t, ntc, r, ep, m_cur, n_next, n, wt, vec, src, dst, w,
-                                    sm);
+                compact_wtile<false>(ws, c, t, ntc, r, ep, m_cur, n_next, n, wt, src, dst, w);
         }
         ep++;
+        mark_work(c);
         grid_sync(ws.bar, gen, status);
+        log_phase(c, PH_COMPACT, r);
         const uint32_t m_next = ntc ? ld_volatile_u32(&c->m_next) : 0u;
         if (gtid == 0 && r + 1 <= (uint32_t)kMaxRounds) {
             c->stat_m[r + 1] = m_next;
@@ -540,7 +599,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
     for (uint32_t t = bid; t < nte; t += nb)
         emit_tile(ws, c, t, nte, ep, words, cap, out, sm);
     ep++;
+    mark_work(c);
     grid_sync(ws.bar, gen, status);
+    log_phase(c, PH_EMIT, r);
     if (gtid == 0) {
         finish(c, out_count, nte ? ld_volatile_u32(&c->emitted) : 0u, n, n_cur);
         c->round = r + 1;
@@ -595,20 +656,29 @@ __global__ void __launch_bounds__(kThreads) k_find0(Ws ws)
                 (size_t)gridDim.x * blockDim.x);
 }
 
+// Takes the next tile index for the calling warp from *ticket.
+__device__ __forceinline__ uint32_t next_warp_tile(uint32_t *ticket)
+{
+    uint32_t t = 0;
+    if ((threadIdx.x & 31) == 0)
+        t = atomicAdd(ticket, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
 template <bool R0>
 __global__ void __launch_bounds__(kThreads) k_hook(Ws ws)
 {
-    __shared__ TileSmem sm;
+    __shared__ uint32_t s_flag;
     Ctl *c = ws.ctl;
     const uint32_t round = c->round, epoch = c->epoch, n_cur = c->n_cur;
-    const uint32_t ntiles = (n_cur + kTile - 1) / kTile;
+    const uint32_t ntiles = (n_cur + kHookWTile - 1) / kHookWTile;
     for (;;) {
-        const uint32_t tile = next_tile(&c->ticket, &sm.s_tile);
+        const uint32_t tile = next_warp_tile(&c->ticket);
         if (tile >= ntiles)
             break;
-        hook_tile<R0>(ws, c, tile, ntiles, round, epoch, n_cur, c->src, c->dst, sm);
+        hook_wtile<R0>(ws, c, tile, ntiles, round, epoch, n_cur, c->src, c->dst);
     }
-    if (last_block_done(&c->done, &sm.s_flag) && threadIdx.x == 0) {
+    if (last_block_done(&c->done, &s_flag) && threadIdx.x == 0) {
         if (ntiles == 0)
             c->n_next = 0;
         c->epoch = epoch + 1;
@@ -649,18 +719,18 @@ template <bool R0>
 __global__ void __launch_bounds__(kThreads)
 k_compact(Ws ws, cudaGraphConditionalHandle loop, uint32_t graph_mode)
 {
-    __shared__ TileSmem sm;
+    __shared__ uint32_t s_flag;
     Ctl *c = ws.ctl;
     const uint32_t round = c->round, epoch = c->epoch, m_cur = c->m_cur, n_next = c->n_next;
-    const uint32_t ntiles = (m_cur + kTile - 1) / kTile;
+    const uint32_t ntiles = (m_cur + kCompWTile - 1) / kCompWTile;
     for (;;) {
-        const uint32_t tile = next_tile(&c->ticket, &sm.s_tile);
+        const uint32_t tile = next_warp_tile(&c->ticket);
         if (tile >= ntiles)
             break;
-        compact_tile<R0>(ws, c, tile, ntiles, round, epoch, m_cur, n_next, c->n, c->wt, c->vec_ok,
-                         c->src, c->dst, (const uint32_t *)c->w, sm);
+        compact_wtile<R0>(ws, c, tile, ntiles, round, epoch, m_cur, n_next, c->n, c->wt, c->src,
+                          c->dst, (const uint32_t *)c->w);
     }
-    if (last_block_done(&c->done, &sm.s_flag) && threadIdx.x == 0) {
+    if (last_block_done(&c->done, &s_flag) && threadIdx.x == 0) {
         const uint32_t m_next = ntiles ? ld_volatile_u32(&c->m_next) : 0u;
         const uint32_t r1 = round + 1;
         if (r1 <= (uint32_t)kMaxRounds) {
@@ -713,8 +783,8 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 static uint32_t desc_capacity(uint32_t n_cap, uint32_t m_cap)
 {
     const uint32_t words = (m_cap + 31) / 32;
-    uint32_t t = (m_cap + kTile - 1) / kTile;
-    t = t > (n_cap + kTile - 1) / kTile ? t : (n_cap + kTile - 1) / kTile;
+    uint32_t t = (m_cap + kCompWTile - 1) / kCompWTile;
+    t = t > (n_cap + kHookWTile - 1) / kHookWTile ? t : (n_cap + kHookWTile - 1) / kHookWTile;
     t = t > (words + kEmitWords - 1) / kEmitWords ? t : (words + kEmitWords - 1) / kEmitWords;
     return t + 1;
 }
@@ -1024,6 +1094,65 @@ cudaError_t single_profile(Single &s, const int32_t *src, const int32_t *dst, co
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return err;
+}
+
+// Per-phase times of the last fused solve, from its phase log (measured
+// inside the timed kernel: %globaltimer at each grid barrier), with the
+// algorithmic bytes of each phase kind from the per-round sizes.
+cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<KernelProfile> &prof)
+{
+    prof.clear();
+    MST_TRY(cudaStreamSynchronize(stream));
+    Ctl c;
+    MST_TRY(cudaMemcpy(&c, s.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    static const char *names[] = {"start", "init", "find0", "hook", "compress", "compact", "emit"};
+    const double n = c.n, m = c.m;
+    auto bytes_of = [&](int kind, uint32_t r) -> double {
+        switch (kind) {
+        case PH_INIT: return 8.0 * n + m / 8.0;
+        case PH_FIND0: return 12.0 * m;
+        case PH_HOOK: return 20.0 * c.stat_n[r] + 4.0 * c.stat_n[r + 1];
+        case PH_COMPRESS: return 0.0;  // attributed once per round below
+        case PH_COMPACT: return (r == 0 ? 12.0 : 16.0) * c.stat_m[r] + 16.0 * c.stat_m[r + 1];
+        case PH_EMIT: return m / 8.0 + 4.0 * (n > 0 ? n - 1 : 0);
+        }
+        return 0.0;
+    };
+    const uint32_t np = c.nphase < (uint32_t)kMaxPhaseLog ? c.nphase : (uint32_t)kMaxPhaseLog;
+    auto add = [&](const std::string &name, double ms, double bytes) {
+        for (auto &k : prof)
+            if (k.name == name) {
+                k.launches++;
+                k.ms += ms;
+                k.bytes += bytes;
+                return;
+            }
+        prof.push_back(KernelProfile{name, 1, ms, bytes});
+    };
+    uint32_t last_compress_round = 0xffffffffu;
+    double wait_ms = 0.0;
+    int waits = 0;
+    for (uint32_t i = 1; i < np; i++) {
+        const int k = c.phase_kind[i] < 7 ? c.phase_kind[i] : 0;
+        const uint32_t r = c.phase_round[i];
+        const double ms = (double)(c.phase_ns[i] - c.phase_ns[i - 1]) * 1e-6;
+        double b = bytes_of(k, r < (uint32_t)kMaxRounds ? r : 0);
+        if (k == PH_COMPRESS && r != last_compress_round) {
+            b = 8.0 * c.stat_n[r] + 4.0 * c.stat_n[r + 1];
+            last_compress_round = r;
+        }
+        std::string name = std::string("k_solve:") + names[k];
+        if (k == PH_HOOK || k == PH_COMPRESS || k == PH_COMPACT)
+            name += r == 0 ? "@r0" : "@r1+";
+        add(name, ms, b);
+        if (c.work_ns[i] > c.phase_ns[i - 1] && c.work_ns[i] <= c.phase_ns[i]) {
+            wait_ms += (double)(c.phase_ns[i] - c.work_ns[i]) * 1e-6;
+            waits++;
+        }
+    }
+    if (waits)
+        prof.push_back(KernelProfile{"(of which CTA 0 waits at barriers)", waits, wait_ms, 0.0});
+    return cudaSuccess;
 }
 
 // Algorithmic DRAM bytes of a whole solve from its per-round sizes: the

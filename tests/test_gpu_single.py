@@ -274,10 +274,34 @@ def test_profile_replay_matches(handle):
     s, d, w = to_dev(g.src, g.dst, g.w)  # kept alive: the replay reuses these buffers
     out = torch.full((g.n - 1,), -1, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert B.mst_set_single_schedule(handle, 2, 0) == B.MST_OK
+    try:
+        assert B.mst_solve(handle, g.n, g.m, s, d, w, out, cnt) == B.MST_OK
+        first = out.clone()
+        prof = B.mst_profile_last_solve(handle)
+        assert torch.equal(first, out)  # the replay writes the same tree again
+        names = [p["name"] for p in prof]
+        assert "k_find0" in names and "k_compact<R0>" in names and "k_emit" in names
+        assert all(p["total_ms"] > 0 and p["launches"] >= 1 for p in prof)
+    finally:
+        B.mst_set_single_schedule(handle, 0, 0)
+
+
+def test_fused_phase_log(handle):
+    g = gg.random_connected(50000, 200000, 29)
+    s, d, w = to_dev(g.src, g.dst, g.w)
+    out = torch.full((g.n - 1,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert B.mst_set_single_schedule(handle, 1, 0) == B.MST_OK
     assert B.mst_solve(handle, g.n, g.m, s, d, w, out, cnt) == B.MST_OK
-    first = out.clone()
     prof = B.mst_profile_last_solve(handle)
-    assert torch.equal(first, out)  # the replay writes the same tree again
-    names = [p["name"] for p in prof]
-    assert "k_find0" in names and "k_compact<R0>" in names and "k_emit" in names
-    assert all(p["total_ms"] > 0 and p["launches"] >= 1 for p in prof)
+    rounds = len(B.mst_get_round_stats(handle)[0]) - 1
+
+    def count(kind):
+        return sum(p["launches"] for p in prof if p["name"].startswith("k_solve:" + kind))
+
+    assert count("find0") == 1 and count("emit") == 1 and count("init") == 1
+    assert count("hook") == rounds == count("compact")
+    assert count("compress") >= rounds
+    assert all(p["total_ms"] > 0 for p in prof)
+    B.mst_set_single_schedule(handle, 0, 0)

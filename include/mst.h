@@ -204,6 +204,35 @@ mst_status mst_autotune_batched(mst_handle h, mst_weight_type wt, int32_t G,
                                 int32_t *out_edge_ids, int64_t *out_counts,
                                 const char *cache_path, void *stream);
 
+/*
+ * Allocation-free solve of one small graph, for callers that cannot
+ * allocate device memory when they solve: code inside a CUDA graph being
+ * captured, hosts that hand out device memory once at start-up, processes
+ * whose device memory a framework allocator already holds.  The paper has
+ * no counterpart; it is a deployment form of the same rounds.
+ *   Takes no handle and calls no cudaMalloc, cudaFree or allocating
+ *   library routine.  One thread block solves the graph on `stream`, with
+ *   its working arrays in shared memory or in a fixed scratch array that the
+ *   library declares at file scope: every GPU that loads the library holds
+ *   that array (about 5.9 MB) until the process exits.
+ *   Limits: n <= 65536 and m <= 262144; larger graphs return MST_ERR_BUDGET
+ *   before anything is queued.
+ *   Arguments as in mst_solve_ex (device pointers, current device).
+ *   out_status: optional device int32 (NULL = none) receiving the device
+ *   outcome as an mst_status (MST_OK, MST_ERR_DISCONNECTED,
+ *   MST_ERR_INVALID_ARG for a bad vertex id or NaN, MST_ERR_INTERNAL).
+ *   The first call on a device looks up the scratch array's device address
+ *   and sets the kernel's shared-memory limit; make that first call outside
+ *   any stream capture.  All calls share the one array, which keeps the last
+ *   call's contents (the kernel clears what must start empty): calls that
+ *   may overlap on the GPU (other streams, other host threads) race on it
+ *   and must be serialised by the caller.
+ */
+mst_status mst_solve_noalloc(mst_weight_type wt, int32_t n, int64_t m,
+                             const int32_t *src, const int32_t *dst, const void *w,
+                             int32_t *out_edge_ids, int64_t *out_count, int32_t *out_status,
+                             void *stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /*

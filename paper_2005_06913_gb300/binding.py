@@ -51,6 +51,7 @@ _SIGS = {
     "mst_set_single_schedule": (_INT, [_P, _INT, _INT]),
     "mst_autotune_batched": (_INT, [_P, _INT, _I32, _P, _P, _I64, _I64, _P, _P, _P, _P, _P,
                                     ctypes.c_char_p, _P]),
+    "mst_solve_noalloc": (_INT, [_INT, _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "mst_server_start": (_INT, [_P, _INT, _INT]),
     "mst_submit": (_INT, [_P, _INT, _I32, _I64, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "mst_poll": (_INT, [_P, ctypes.c_uint64, ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_double)]),
@@ -84,7 +85,7 @@ def lib() -> ctypes.CDLL:
 def header_symbols() -> list:
     """Function names declared in include/mst.h."""
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(mst_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^(?:mst_status|const\s+char\s*\*)\s*(mst_\w+)\s*\(", text, re.M)))
 
 
 def _ptr(x) -> int:
@@ -195,6 +196,14 @@ def mst_autotune_batched(h, wt, G, vtx_off, edge_off, total_n, total_m, src, dst
     return lib().mst_autotune_batched(h, int(wt), int(G), _ptr(vtx_off), _ptr(edge_off),
                                       int(total_n), int(total_m), _ptr(src), _ptr(dst), _ptr(w),
                                       _ptr(out_edge_ids), _ptr(out_counts), cp, _stream(stream))
+
+
+def mst_solve_noalloc(wt, n, m, src, dst, w, out_edge_ids, out_count, out_status=None,
+                      stream=None) -> int:
+    """Allocation-free solve of one small graph (no handle; see mst.h)."""
+    return lib().mst_solve_noalloc(int(wt), int(n), int(m), _ptr(src), _ptr(dst), _ptr(w),
+                                   _ptr(out_edge_ids), _ptr(out_count), _ptr(out_status),
+                                   _stream(stream))
 
 
 def mst_server_start(h, streams: int = 4, max_batch: int = 256) -> int:

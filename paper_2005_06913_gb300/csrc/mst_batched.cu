@@ -982,4 +982,143 @@ cudaError_t batched_autotune(Batched &b, int device, uint32_t wt, int32_t G,
     return cudaSuccess;
 }
 
+// ------------------------------------------------- allocation-free solve
+
+// Some callers cannot allocate device memory at solve time: code running
+// inside a CUDA graph being captured, a real-time or plugin host whose
+// memory is handed out once at start-up, or a process whose device memory
+// is fully reserved by a framework allocator.  mst_solve_noalloc serves
+// them: one CTA runs every Boruvka round of one graph (the batched solver's
+// per-graph team), with its working arrays in this file-scope device array
+// instead of a handle's workspace.  Every GPU that loads the library holds
+// the array until the process exits; every call shares it and it keeps the
+// last call's contents, so the kernel clears what must start empty, and
+// calls that overlap on the GPU (different streams, or different host
+// threads) race on it.
+constexpr uint32_t kNoAllocMaxN = 65536;
+constexpr uint32_t kNoAllocMaxM = 262144;
+constexpr size_t kNoAllocEdgeBytes = (size_t)kNoAllocMaxM * 16;
+constexpr size_t kNoAllocVtxBytes = 2 * (size_t)kNoAllocMaxN * 8 + 3 * (size_t)kNoAllocMaxN * 4;
+constexpr size_t kNoAllocBitsBytes = ((size_t)kNoAllocMaxM / 32 + 1) * 4;
+constexpr size_t kNoAllocBytes = 256 + kNoAllocEdgeBytes + kNoAllocVtxBytes + kNoAllocBitsBytes;
+constexpr int kNoAllocThreads = 1024;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Lays a graph's working arrays out: in shared memory when they fit (as
+// the batched solver does), else in the scratch array.  The first 256
+// bytes of the scratch hold the status word.
+__device__ __forceinline__ GraphArrays place_noalloc(unsigned char *scratch, char *sm,
+                                                     size_t budget, uint32_t n, uint32_t m)
+{
+    GraphArrays A;
+    const size_t vb = vbytes_of(n, m), eb = ebytes_of(m);
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    char *p = (vb <= budget) ? sm : (char *)scratch + 256 + kNoAllocEdgeBytes;
+    A.mA = (unsigned long long *)p;
+    p += al((size_t)n * 8);
+    A.mB = (unsigned long long *)p;
+    p += al((size_t)n * 8);
+    A.parent = (int32_t *)p;
+    p += al((size_t)n * 4);
+    A.nid = (int32_t *)p;
+    p += al((size_t)n * 4);
+    A.lab = (int32_t *)p;
+    p += al((size_t)n * 4);
+    A.bits = (uint32_t *)p;
+    p += al((((size_t)m + 31) / 32) * 4);
+    A.E = (vb + eb <= budget) ? (uint4 *)p : (uint4 *)(scratch + 256);
+    return A;
+}
+
+__global__ void __launch_bounds__(kNoAllocThreads)
+k_noalloc(unsigned char *scratch, uint32_t smem_bytes, const int32_t *src, const int32_t *dst,
+          const uint32_t *w, uint32_t wt, uint32_t n, uint32_t m, int32_t *out,
+          int64_t *out_count, int32_t *out_status)
+{
+    extern __shared__ __align__(16) char smem[];
+    __shared__ uint32_t scratch_words[4 * (kNoAllocThreads / 32) + 2];
+    uint32_t *status = (uint32_t *)scratch;
+    if (threadIdx.x == 0)
+        *status = 0u;  // the previous call's outcome must not leak into this one
+    __syncthreads();
+    BlockTeam<kNoAllocThreads> team{scratch_words};
+    const GraphArrays A = place_noalloc(scratch, smem, smem_bytes, n, m);
+    solve_graph(team, n, m, src, dst, w, wt, A, out, out_count, status);
+    if (threadIdx.x == 0 && out_status) {
+        const uint32_t b = *(volatile uint32_t *)status;
+        int32_t code = MST_OK;
+        if (b & ST_INTERNAL)
+            code = MST_ERR_INTERNAL;
+        else if (b & (ST_BAD_VERTEX | ST_NAN))
+            code = MST_ERR_INVALID_ARG;
+        else if (b & ST_DISCONNECTED)
+            code = MST_ERR_DISCONNECTED;
+        *out_status = code;
+    }
+}
+
+// Device address of the scratch array, looked up once per device with that
+// device current (in host code the array's name is only a host stand-in).
+static std::mutex g_noalloc_mu;
+static std::map<int, unsigned char *> g_noalloc_ptr;
+static std::map<int, uint32_t> g_noalloc_smem;
+
+static cudaError_t noalloc_setup(int device, unsigned char **ptr, uint32_t *smem)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_ptr.find(device);
+    if (it != g_noalloc_ptr.end()) {
+        *ptr = it->second;
+        *smem = g_noalloc_smem[device];
+        return cudaSuccess;
+    }
+    void *p = nullptr;
+    MST_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    int optin = 0;
+    MST_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    const uint32_t bytes = (uint32_t)((optin - 2048) & ~255);
+    MST_TRY(cudaFuncSetAttribute(k_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    g_noalloc_ptr[device] = (unsigned char *)p;
+    g_noalloc_smem[device] = bytes;
+    *ptr = (unsigned char *)p;
+    *smem = bytes;
+    return cudaSuccess;
+}
+
+}  // namespace mst
+
+extern "C" mst_status mst_solve_noalloc(mst_weight_type wt, int32_t n, int64_t m,
+                                        const int32_t *src, const int32_t *dst, const void *w,
+                                        int32_t *out_edge_ids, int64_t *out_count,
+                                        int32_t *out_status, void *stream)
+{
+    using namespace mst;
+    if ((wt != MST_W_U32 && wt != MST_W_F32) || n < 0 || m < 0 || !out_count)
+        return MST_ERR_INVALID_ARG;
+    if (m > 0 && (!src || !dst || !w))
+        return MST_ERR_INVALID_ARG;
+    if (n > 1 && !out_edge_ids)
+        return MST_ERR_INVALID_ARG;
+    if (n == 0 && m > 0)
+        return MST_ERR_INVALID_ARG;
+    if ((uint64_t)n > kNoAllocMaxN || (uint64_t)m > kNoAllocMaxM)
+        return MST_ERR_BUDGET;  // beyond the fixed scratch
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess)
+        return MST_ERR_CUDA;
+    unsigned char *scratch = nullptr;
+    uint32_t smem = 0;
+    if (noalloc_setup(device, &scratch, &smem) != cudaSuccess) {
+        cudaGetLastError();
+        return MST_ERR_CUDA;
+    }
+    k_noalloc<<<1, kNoAllocThreads, smem, (cudaStream_t)stream>>>(
+        scratch, smem, src, dst, (const uint32_t *)w, (uint32_t)wt, (uint32_t)n, (uint32_t)m,
+        out_edge_ids, out_count, out_status);
+    return cudaGetLastError() == cudaSuccess ? MST_OK : MST_ERR_CUDA;
+}
+
+namespace mst {
+
 }  // namespace mst

@@ -8,7 +8,9 @@ emit) with the inputs already resident in HBM.  The 25 MB input fits in the
 the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config 1|2|3] [--no-cpu-baseline]
+                  [--config 1|2|3] [--no-cpu-baseline] [--schedule fused|graph]
+  python bench.py --workload batched [--graphs G]     # C4: G graphs in one launch
+  python bench.py --workload serving [--pool P] [--rates 1000,5000] [--seconds S]
 
 Under torchrun (N > 1) every rank solves its own replica of the workload (a
 single solve does not shard); value = edges of all ranks / max rank time.
@@ -360,6 +362,243 @@ def run_ours(args):
     return 0
 
 
+def _percentiles(xs):
+    xs = sorted(xs)
+    if not xs:
+        return None, None
+    pick = lambda q: xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+    return pick(0.50), pick(0.99)
+
+
+def run_batched(args):
+    """C4: G independent random connected graphs (n log-uniform in
+    [64, 65536], average degree 8) solved by one mst_solve_batched launch
+    per step, against the same graphs solved one launch per graph: the
+    batched kernel with G = 1, and the single-graph fused kernel."""
+    import torch
+
+    from paper_2005_06913_gb300 import binding as B
+    from paper_2005_06913_gb300 import build as build_mod
+    from paper_2005_06913_gb300 import graphgen as gg
+    from paper_2005_06913_gb300.sharding import shard_graphs, sub_batch
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build_mod.build()
+    if dist is not None:
+        dist.barrier()
+    full = gg.batched(args.graphs, 64, 65536, 8, gg.SEED_BASE + 3)
+    mine = shard_graphs(np.diff(full.edge_off), ws, rank) if ws > 1 else np.arange(full.G)
+    b = sub_batch(full, mine) if ws > 1 else full
+    tn, tm = int(b.vtx_off[-1]), int(b.edge_off[-1])
+    dev = lambda a: torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).cuda()
+    vo, eo, s, d, w = dev(b.vtx_off), dev(b.edge_off), dev(b.src), dev(b.dst), dev(b.w)
+    out = torch.empty(max(tn, 1), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(max(b.G, 1), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = B.mst_create(torch.cuda.current_device(), 0)
+    st = B.mst_autotune_batched(h, B.MST_W_U32, b.G, vo, eo, tn, tm, s, d, w, out, cnt, None, stream)
+    if st != B.MST_OK:
+        raise B.MstError(st, "autotune")
+
+    def solve_batch():
+        st = B.mst_solve_batched(h, B.MST_W_U32, b.G, vo, eo, tn, tm, s, d, w, out, cnt, stream)
+        if st != B.MST_OK:
+            raise B.MstError(st, "mst_solve_batched")
+
+    for _ in range(max(args.warmup, 3)):
+        solve_batch()
+    status = B.mst_get_status(h, stream)
+    counts = cnt.cpu().numpy()
+    if status != B.MST_OK or not np.array_equal(counts, np.diff(b.vtx_off) - 1):
+        raise RuntimeError(f"batched self-check failed: {B.mst_status_string(status)}")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(torch.cuda.current_device()).start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for a, z in ev:
+        a.record(stream)
+        solve_batch()
+        z.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    clk.mark(t0, t1)
+    clk.stop()
+    lat = [a.elapsed_time(z) for a, z in ev]
+    total_ms = sum(lat)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    p50, p99 = _percentiles(lat)
+    line = {
+        "metric": "batched graphs/s (p50/p99 batch latency)", "impl": "ours",
+        "value": ws * full.G / ws * args.steps / (total_ms * 1e-3) if ws > 1
+        else b.G * args.steps / (total_ms * 1e-3),
+        "unit": "graphs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"C4 batched: {full.G} random connected graphs, n log-uniform "
+                               f"[64, 65536], degree 8", "graphs": full.G,
+                   "total_vertices": int(full.vtx_off[-1]), "total_edges": int(full.edge_off[-1]),
+                   "l2": "inputs larger than L2", "parallelism":
+                   f"graphs sharded over {ws} ranks (longest-first)" if ws > 1 else "single GPU"},
+        "latency_ms": {"p50": p50, "p99": p99, "note": "every graph of a batch completes with it"},
+        "edges_per_s": tm * args.steps / (total_ms * 1e-3),
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1:
+        # the same graphs, one launch per graph: (a) the batched kernel with
+        # G = 1, (b) the single-graph fused kernel
+        sub = list(range(0, b.G, max(1, b.G // args.per_graph_sample)))
+        per_a, per_b = [], []
+        vo1 = torch.zeros(2, dtype=torch.int64, device="cuda")
+        eo1 = torch.zeros(2, dtype=torch.int64, device="cuda")
+        for g in sub:
+            n_g = int(b.vtx_off[g + 1] - b.vtx_off[g])
+            m_g = int(b.edge_off[g + 1] - b.edge_off[g])
+            e0, v0 = int(b.edge_off[g]), int(b.vtx_off[g])
+            vo1[1] = n_g
+            eo1[1] = m_g
+            for which, sink in ((0, per_a), (1, per_b)):
+                fn = (lambda: B.mst_solve_batched(h, B.MST_W_U32, 1, vo1, eo1, n_g, m_g,
+                                                  s[e0:], d[e0:], w[e0:], out[v0:], cnt[g:], stream)) \
+                    if which == 0 else \
+                    (lambda: B.mst_solve(h, n_g, m_g, s[e0:], d[e0:], w[e0:], out[v0:], cnt[g:],
+                                         stream))
+                fn()
+                a_, z_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                fn()
+                z_.record(stream)
+                torch.cuda.synchronize()
+                sink.append(a_.elapsed_time(z_))
+        scale = b.G / len(sub)
+        for name, xs in (("batched_kernel_one_graph_per_launch", per_a),
+                         ("single_graph_kernel_one_graph_per_launch", per_b)):
+            q50, q99 = _percentiles(xs)
+            line[name] = {"graphs_per_s": len(xs) / (sum(xs) * 1e-3),
+                          "est_ms_for_all_graphs": sum(xs) * scale,
+                          "latency_ms": {"p50": q50, "p99": q99},
+                          "sample": f"{len(xs)} of {b.G} graphs (every {b.G // len(sub)}th)"}
+        line["speedup_vs_one_launch_per_graph"] = line["value"] / max(
+            line["batched_kernel_one_graph_per_launch"]["graphs_per_s"],
+            line["single_graph_kernel_one_graph_per_launch"]["graphs_per_s"])
+    B.mst_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_serving(args):
+    """C5-shaped serving: a pool of random connected graphs (n log-uniform
+    in [1024, nmax], degree 6, float32 weights) replayed as an open-loop
+    Poisson stream at each rate for `seconds`; the continuous-batching
+    server admits requests as streams and memory free up.  Reports graphs/s
+    completed and p50/p99 request latency, and the same stream served one
+    solve at a time (single-graph kernel, one stream) for comparison."""
+    import torch
+
+    from paper_2005_06913_gb300 import binding as B
+    from paper_2005_06913_gb300 import build as build_mod
+    from paper_2005_06913_gb300 import graphgen as gg
+
+    torch.cuda.set_device(0)
+    build_mod.build()
+    pool = gg.serving_pool(args.pool, 1024, args.serve_nmax, 6, gg.SEED_BASE + 4)
+    dev = lambda a: torch.from_numpy(a.view(np.int32) if a.dtype != np.int64 else a).cuda()
+    s, d, w = dev(pool.src), dev(pool.dst), dev(pool.w)
+    nmax = int(np.diff(pool.vtx_off).max())
+    ring = int(max(64, min(4096, (2 << 30) // (nmax * 4))))  # in-flight requests (2 GiB of outputs)
+    outs = torch.empty((ring, nmax), dtype=torch.int32, device="cuda")
+    cnts = torch.zeros(ring, dtype=torch.int64, device="cuda")
+    rng = np.random.default_rng(5)
+    budget = 120 << 30
+    results = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        h = B.mst_create(0, budget)
+        B.mst_server_start(h, args.streams, args.max_batch)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * args.seconds) + 1))
+        arrivals = arrivals[arrivals < args.seconds]
+        picks = rng.integers(0, pool.G, arrivals.shape[0])
+        tickets, lat, done_t = {}, [], []
+        slot_busy = {}
+        t_start = time.perf_counter()
+        k = 0
+        while k < arrivals.shape[0] or tickets:
+            now = time.perf_counter() - t_start
+            while k < arrivals.shape[0] and arrivals[k] <= now:
+                slot = k % ring
+                if slot in slot_busy:  # ring full: the stream is overloaded, wait
+                    break
+                g = int(picks[k])
+                e0, e1 = int(pool.edge_off[g]), int(pool.edge_off[g + 1])
+                n_g = int(pool.vtx_off[g + 1] - pool.vtx_off[g])
+                st, t = B.mst_submit(h, B.MST_W_F32, n_g, e1 - e0, s[e0:], d[e0:], w[e0:],
+                                     outs[slot], cnts[slot:])
+                tickets[t] = (slot, n_g)
+                slot_busy[slot] = t
+                k += 1
+            for t in list(tickets):
+                st, dn, l_us = B.mst_poll(h, t)
+                if dn:
+                    slot, n_g = tickets.pop(t)
+                    slot_busy.pop(slot, None)
+                    lat.append(l_us * 1e-3)
+                    done_t.append(time.perf_counter() - t_start)
+            time.sleep(0.0002)
+        elapsed = max(done_t) if done_t else 1.0
+        B.mst_server_stop(h)
+        B.mst_destroy(h)
+        p50, p99 = _percentiles(lat)
+        results.append({"rate_offered": rate, "requests": len(lat),
+                        "graphs_per_s": len(lat) / elapsed, "latency_ms": {"p50": p50, "p99": p99}})
+    # one solve at a time on one stream, same pool, back to back (its best case)
+    h = B.mst_create(0, 0)
+    one = []
+    for g in range(min(pool.G, 64)):
+        e0, e1 = int(pool.edge_off[g]), int(pool.edge_off[g + 1])
+        n_g = int(pool.vtx_off[g + 1] - pool.vtx_off[g])
+        a_, z_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        B.mst_solve_ex(h, B.MST_W_F32, n_g, e1 - e0, s[e0:], d[e0:], w[e0:], outs[0], cnts[0:])
+        a_.record()
+        B.mst_solve_ex(h, B.MST_W_F32, n_g, e1 - e0, s[e0:], d[e0:], w[e0:], outs[0], cnts[0:])
+        z_.record()
+        torch.cuda.synchronize()
+        one.append(a_.elapsed_time(z_))
+    B.mst_destroy(h)
+    q50, q99 = _percentiles(one)
+    best = max(results, key=lambda r: r["graphs_per_s"])
+    line = {"metric": "served graphs/s at p50/p99 latency", "impl": "ours",
+            "value": best["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"C5-shaped serving: pool of {pool.G} random connected graphs, "
+                                   f"n log-uniform [1024, {args.serve_nmax}], degree 6, float32 "
+                                   f"weights; open-loop Poisson arrivals for {args.seconds} s per rate",
+                       "streams": args.streams, "max_batch": args.max_batch,
+                       "memory_budget_bytes": budget},
+            "sweep": results,
+            "one_solve_at_a_time": {"graphs_per_s": len(one) / (sum(one) * 1e-3),
+                                    "latency_ms": {"p50": q50, "p99": q99},
+                                    "sample": f"first {len(one)} pool graphs, back to back"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,11 +610,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", choices=["fused", "graph"], default="fused")
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
+    ap.add_argument("--graphs", type=int, default=4096)
+    ap.add_argument("--per-graph-sample", type=int, default=256)
+    ap.add_argument("--pool", type=int, default=128)
+    ap.add_argument("--serve-nmax", type=int, default=1048576)
+    ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000")
+    ap.add_argument("--seconds", type=float, default=5.0)
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--max-batch", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -117,7 +117,11 @@ template <int T>
 struct BlockTeam {
     static constexpr int kSize = T;
     static constexpr int kW = T / 32;
-    uint32_t *scratch;  // 4*kW + 2 words of shared memory
+    static constexpr int kWarps = T / 32;
+    uint32_t *scratch;             // 4*kW + 2 words of shared memory
+    unsigned long long *ring;      // kRing look-back slots in shared memory
+    uint32_t *total;               // one shared word: a phase's total
+    __device__ __forceinline__ int warp() const { return threadIdx.x >> 5; }
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
     __device__ __forceinline__ bool any(bool x) const { return __syncthreads_or(x ? 1 : 0) != 0; }
@@ -218,6 +222,8 @@ struct BlockTeam {
 // One warp.
 struct WarpTeam {
     static constexpr int kSize = 32;
+    static constexpr int kWarps = 1;
+    __device__ __forceinline__ int warp() const { return 0; }
     __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
     __device__ __forceinline__ void sync() const { __syncwarp(); }
     __device__ __forceinline__ bool any(bool x) const { return __any_sync(0xffffffffu, x) != 0; }
@@ -297,6 +303,119 @@ __device__ __forceinline__ bool chase_v(volatile int32_t *parent, uint32_t start
     return false;
 }
 
+// ---------------------------------------------------- warp tiles in a team
+//
+// Inside a CTA team each warp owns tiles w, w + W, w + 2W, ... of a phase
+// and takes its output offset from a decoupled look-back over a ring of
+// kRing descriptors in shared memory (tagged with the tile number).  Tiles
+// cannot run more than about W ahead of the slowest unfinished one (each
+// waits on its predecessors' aggregates, and a warp's previous tile is W
+// back), and the nearest inclusive prefix is at most W back, so a ring of
+// 4W slots is never overwritten while still needed.  A one-warp team needs
+// no look-back: it keeps a running offset.
+constexpr uint32_t kRing = 128;
+constexpr int kTeamHookIpl = 4, kTeamCompIpl = 8;
+
+__device__ __forceinline__ unsigned long long ring_word(uint32_t tile, uint32_t flag, uint32_t v)
+{
+    return ((unsigned long long)(tile + 1) << 32) | ((unsigned long long)flag << 30) |
+           (v & 0x3fffffffu);
+}
+
+__device__ __forceinline__ uint32_t lookback_ring(unsigned long long *ring, uint32_t tile,
+                                                  uint32_t aggregate, uint32_t *status)
+{
+    const int lane = threadIdx.x & 31;
+    volatile unsigned long long *rv = ring;
+    if (tile == 0) {
+        if (lane == 0)
+            rv[0] = ring_word(0, 2u, aggregate);
+        __syncwarp();
+        return 0;
+    }
+    if (lane == 0)
+        rv[tile % kRing] = ring_word(tile, 1u, aggregate);
+    uint32_t excl = 0;
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t idx = (int64_t)tile - 1 - lane;
+        uint32_t flag = 2u, val = 0u;
+        if (idx >= 0) {
+            const unsigned long long d = rv[(uint32_t)idx % kRing];
+            const bool mine = (uint32_t)(d >> 32) == (uint32_t)idx + 1u;
+            flag = mine ? (uint32_t)((d >> 30) & 3u) : 0u;
+            val = (uint32_t)(d & 0x3fffffffu);
+        }
+        const uint32_t pmask = __ballot_sync(0xffffffffu, flag == 2u);
+        const uint32_t zmask = __ballot_sync(0xffffffffu, flag == 0u);
+        const uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 32u;
+        const uint32_t need = stop == 32u ? 0xffffffffu : ((2u << stop) - 1u);
+        if (stop == 32u || (zmask & need)) {  // wait (a prefix is always within 32 back)
+            if (++spins > kSpinLimit) {
+                if (lane == 0)
+                    atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(20);
+            continue;
+        }
+        uint32_t part = ((uint32_t)lane <= stop) ? val : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+        excl = part;
+        break;
+    }
+    if (lane == 0)
+        rv[tile % kRing] = ring_word(tile, 2u, excl + aggregate);
+    __syncwarp();
+    return excl;
+}
+
+// A phase's exclusive offset for one warp tile: running offset for a
+// one-warp team, ring look-back otherwise.
+template <class Team>
+__device__ __forceinline__ uint32_t tile_offset(const Team &tm, uint32_t tile, uint32_t total,
+                                                uint32_t &run, uint32_t *status);
+
+template <int T>
+__device__ __forceinline__ uint32_t tile_offset(const BlockTeam<T> &tm, uint32_t tile,
+                                                uint32_t total, uint32_t &run, uint32_t *status)
+{
+    (void)run;
+    return lookback_ring(tm.ring, tile, total, status);
+}
+
+template <>
+__device__ __forceinline__ uint32_t tile_offset<WarpTeam>(const WarpTeam &, uint32_t, uint32_t total,
+                                                          uint32_t &run, uint32_t *)
+{
+    const uint32_t ex = run;
+    run += total;
+    return ex;
+}
+
+// Empties the look-back ring before a phase that uses it (after the barrier
+// that ended the previous phase), then waits for the whole team.
+template <int T>
+__device__ __forceinline__ void ring_reset(const BlockTeam<T> &tm)
+{
+    for (uint32_t i = threadIdx.x; i < kRing; i += T)
+        ((volatile unsigned long long *)tm.ring)[i] = 0ull;
+    __syncthreads();
+}
+__device__ __forceinline__ void ring_reset(const WarpTeam &) {}
+
+// Stores a phase total (the owner of the last tile) and reads it after the
+// team barrier.
+template <int T>
+__device__ __forceinline__ void put_total(const BlockTeam<T> &tm, uint32_t v) { *(volatile uint32_t *)tm.total = v; }
+__device__ __forceinline__ void put_total(const WarpTeam &, uint32_t) {}
+template <int T>
+__device__ __forceinline__ uint32_t get_total(const BlockTeam<T> &tm, uint32_t) { return *(volatile uint32_t *)tm.total; }
+__device__ __forceinline__ uint32_t get_total(const WarpTeam &, uint32_t run) { return run; }
+
+
 // All Boruvka rounds of one graph by one team.  Inputs are the graph's slice
 // of the caller's arrays (local ids); A the graph's working arrays.
 template <class Team>
@@ -331,54 +450,80 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
     uint32_t n_r = n, m_r = m;
     unsigned long long *mc = A.mA, *mx = A.mB;
     for (uint32_t r = 0;; r++) {
-        // hook (steps 30-40) and dense renumbering of roots
+        // hook (steps 30-40) and dense renumbering of roots, warp tiles
+        const int lane = threadIdx.x & 31;
+        const uint32_t lt = lanemask_lt();
         uint32_t run = 0;
-        for (uint32_t base = 0; base < n_r; base += TILE) {
-            bool root[4];
-            uint32_t vv[4], rank[4], total;
+        ring_reset(tm);
+        {
+            constexpr uint32_t WT = 32 * kTeamHookIpl;
+            const uint32_t ntiles = (n_r + WT - 1) / WT;
+            for (uint32_t tile = tm.warp(); tile < ntiles; tile += Team::kWarps) {
+                const uint32_t base = tile * WT;
+                unsigned long long k[kTeamHookIpl];
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t v = base + j * T + t;
-                vv[j] = v;
-                root[j] = false;
-                if (v < n_r) {
-                    const unsigned long long k = mc[v];
-                    mx[v] = kNoEdge;
-                    if (k == kNoEdge) {
-                        root[j] = true;
-                    } else {
-                        const uint32_t p = (uint32_t)k;
-                        uint32_t a, b, id;
+                for (int j = 0; j < kTeamHookIpl; j++) {
+                    const uint32_t v = base + j * 32 + lane;
+                    k[j] = v < n_r ? mc[v] : kNoEdge;
+                }
+                uint32_t dd[kTeamHookIpl], id[kTeamHookIpl];
+#pragma unroll
+                for (int j = 0; j < kTeamHookIpl; j++) {
+                    const uint32_t v = base + j * 32 + lane;
+                    if (v < n_r)
+                        mx[v] = kNoEdge;
+                    dd[j] = id[j] = 0;
+                    if (k[j] != kNoEdge) {
+                        const uint32_t p = (uint32_t)k[j];
+                        uint32_t a, b;
                         if (r == 0) {
                             a = (uint32_t)__ldg(src + p);
                             b = (uint32_t)__ldg(dst + p);
-                            id = p;
+                            id[j] = p;
                         } else {
                             const uint4 q = A.E[p];
                             a = q.x;
                             b = q.y;
-                            id = q.w;
+                            id[j] = q.w;
                         }
-                        const uint32_t d = (a == v) ? b : a;
-                        const unsigned long long kd = mc[d];
-                        if ((uint32_t)kd == p && v < d) {
-                            root[j] = true;
+                        dd[j] = (a == v) ? b : a;
+                    }
+                }
+                uint32_t mask[kTeamHookIpl], total = 0;
+#pragma unroll
+                for (int j = 0; j < kTeamHookIpl; j++) {
+                    const uint32_t v = base + j * 32 + lane;
+                    bool root = false;
+                    if (v < n_r) {
+                        const uint32_t d = dd[j];
+                        const unsigned long long kd = k[j] != kNoEdge ? mc[d] : kNoEdge;
+                        if (k[j] == kNoEdge || ((uint32_t)kd == (uint32_t)k[j] && v < d)) {
+                            root = true;
+                            A.parent[v] = (int32_t)v;
                         } else {
                             A.parent[v] = (int32_t)d;
-                            atomicOr(&A.bits[id >> 5], 1u << (id & 31));
+                            atomicOr(&A.bits[id[j] >> 5], 1u << (id[j] & 31));
                         }
                     }
-                    if (root[j])
-                        A.parent[v] = (int32_t)v;
+                    mask[j] = __ballot_sync(0xffffffffu, root);
+                    total += __popc(mask[j]);
+                }
+                const uint32_t ex = tile_offset(tm, tile, total, run, status);
+                if (lane == 0 && tile == ntiles - 1)
+                    put_total(tm, ex + total);
+                uint32_t pos = ex;
+#pragma unroll
+                for (int j = 0; j < kTeamHookIpl; j++) {
+                    if ((mask[j] >> lane) & 1u)
+                        A.nid[base + j * 32 + lane] = (int32_t)(pos + __popc(mask[j] & lt));
+                    pos += __popc(mask[j]);
                 }
             }
-            tm.tile_ranks(root, rank, total);
-#pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (root[j])
-                    A.nid[vv[j]] = (int32_t)(run + rank[j]);
-            run += total;
+            if (ntiles == 0)
+                put_total(tm, 0u);
         }
+        tm.sync();
+        run = get_total(tm, run);
         const uint32_t n_next = run;
         tm.sync();
         // compress: every component takes its root's new id
@@ -408,58 +553,79 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
             }
         }
         tm.sync();
-        // compact in place + find-min of the next round
+        // compact in place + find-min of the next round, warp tiles: a tile's
+        // survivors move only to positions of tiles whose loads are done
+        // (their aggregates were published after their loads)
         run = 0;
-        for (uint32_t base = 0; base < m_r; base += TILE) {
-            bool keep[4];
-            uint4 rec[4];
-            uint32_t rank[4], total;
+        ring_reset(tm);
+        {
+            constexpr uint32_t WT = 32 * kTeamCompIpl;
+            const uint32_t ntiles = (m_r + WT - 1) / WT;
+            const bool filt = 2ull * m_r >= 8ull * (unsigned long long)(n_next ? n_next : 1);
+            for (uint32_t tile = tm.warp(); tile < ntiles; tile += Team::kWarps) {
+                const uint32_t base = tile * WT;
+                uint4 rec[kTeamCompIpl];
+                bool ok[kTeamCompIpl];
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t i = base + j * T + t;
-                keep[j] = false;
-                rec[j] = make_uint4(0, 0, 0, 0);
-                if (i < m_r) {
-                    uint32_t u, v, wb, id;
-                    bool ok;
+                for (int j = 0; j < kTeamCompIpl; j++) {
+                    const uint32_t i = base + j * 32 + lane;
+                    const bool in = i < m_r;
                     if (r == 0) {
-                        u = (uint32_t)__ldg(src + i);
-                        v = (uint32_t)__ldg(dst + i);
-                        ok = u < n && v < n && u != v;
-                        wb = ok ? weight_bits(__ldg(w + i), wt, status) : 0u;
-                        id = i;
+                        const uint32_t u = in ? (uint32_t)__ldg(src + i) : 0u;
+                        const uint32_t v = in ? (uint32_t)__ldg(dst + i) : 0u;
+                        const uint32_t x = in ? __ldg(w + i) : 0u;
+                        ok[j] = in && u < n && v < n && u != v;
+                        rec[j] = make_uint4(u, v, x, i);
                     } else {
-                        const uint4 q = A.E[i];
-                        u = q.x;
-                        v = q.y;
-                        wb = q.z;
-                        id = q.w;
-                        ok = true;
+                        rec[j] = in ? A.E[i] : make_uint4(0, 0, 0, 0);
+                        ok[j] = in;
                     }
-                    if (ok) {
-                        const uint32_t nu = (uint32_t)A.lab[u], nv = (uint32_t)A.lab[v];
+                }
+                uint32_t mask[kTeamCompIpl], total = 0;
+#pragma unroll
+                for (int j = 0; j < kTeamCompIpl; j++) {
+                    bool keep = false;
+                    if (ok[j]) {
+                        const uint32_t nu = (uint32_t)A.lab[rec[j].x], nv = (uint32_t)A.lab[rec[j].y];
                         if (nu >= n_next || nv >= n_next) {
                             atomicOr(status, ST_INTERNAL);
                         } else if (nu != nv) {
-                            keep[j] = true;
-                            rec[j] = make_uint4(nu, nv, wb, id);
+                            keep = true;
+                            rec[j].x = nu;
+                            rec[j].y = nv;
+                            if (r == 0)
+                                rec[j].z = weight_bits(rec[j].z, wt, status);
                         }
                     }
+                    mask[j] = __ballot_sync(0xffffffffu, keep);
+                    total += __popc(mask[j]);
                 }
-            }
-            tm.tile_ranks(keep, rank, total);  // all loads of the tile precede its syncs
+                const uint32_t ex = tile_offset(tm, tile, total, run, status);
+                if (lane == 0 && tile == ntiles - 1)
+                    put_total(tm, ex + total);
+                uint32_t pos = ex;
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (keep[j]) {
-                    const uint32_t pos = run + rank[j];
-                    A.E[pos] = rec[j];
-                    const unsigned long long key = make_key(rec[j].z, pos);
-                    offer_any(&mx[rec[j].x], key);
-                    offer_any(&mx[rec[j].y], key);
+                for (int j = 0; j < kTeamCompIpl; j++) {
+                    if ((mask[j] >> lane) & 1u) {
+                        const uint32_t at = pos + __popc(mask[j] & lt);
+                        A.E[at] = rec[j];
+                        const unsigned long long key = make_key(rec[j].z, at);
+                        if (filt) {
+                            offer_any(&mx[rec[j].x], key);
+                            offer_any(&mx[rec[j].y], key);
+                        } else {
+                            atomicMin(&mx[rec[j].x], key);
+                            atomicMin(&mx[rec[j].y], key);
+                        }
+                    }
+                    pos += __popc(mask[j]);
                 }
             }
-            run += total;
+            if (ntiles == 0)
+                put_total(tm, 0u);
         }
+        tm.sync();
+        run = get_total(tm, run);
         tm.sync();
         m_r = run;
         n_r = n_next;
@@ -606,14 +772,15 @@ __global__ void __launch_bounds__(T) k_b_solve(BWs ws, BJob job)
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ uint32_t scratch[4 * (T / 32) + 2];
-    __shared__ uint32_t s_claim;
+    __shared__ unsigned long long ring[kRing];
+    __shared__ uint32_t s_claim, s_total;
     BCtl *c = ws.ctl;
     if (c->status & ST_BAD_OFFSETS)
         return;
     uint32_t n_big = 0;
     for (int b = 32; b < 64; b++)
         n_big += c->bin_count[b];
-    BlockTeam<T> team{scratch};
+    BlockTeam<T> team{scratch, ring, &s_total};
     // big graphs: one CTA each, largest first
     for (;;) {
         __syncthreads();
@@ -1038,11 +1205,13 @@ k_noalloc(unsigned char *scratch, uint32_t smem_bytes, const int32_t *src, const
 {
     extern __shared__ __align__(16) char smem[];
     __shared__ uint32_t scratch_words[4 * (kNoAllocThreads / 32) + 2];
+    __shared__ unsigned long long ring[kRing];
+    __shared__ uint32_t s_total;
     uint32_t *status = (uint32_t *)scratch;
     if (threadIdx.x == 0)
         *status = 0u;  // the previous call's outcome must not leak into this one
     __syncthreads();
-    BlockTeam<kNoAllocThreads> team{scratch_words};
+    BlockTeam<kNoAllocThreads> team{scratch_words, ring, &s_total};
     const GraphArrays A = place_noalloc(scratch, smem, smem_bytes, n, m);
     solve_graph(team, n, m, src, dst, w, wt, A, out, out_count, status);
     if (threadIdx.x == 0 && out_status) {

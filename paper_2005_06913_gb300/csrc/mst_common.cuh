@@ -28,9 +28,12 @@ constexpr int kChaseLimit = 64;               // pointer hops per thread per pas
 constexpr uint32_t kMaxJumpPasses = 64;       // > log2(2^31): pointer jumping ends sooner
 constexpr uint32_t kSpinLimit = 1u << 22;     // iterations of any device wait
 constexpr int kMaxPhaseLog = 256;             // phase-log entries kept per fused solve
+constexpr uint32_t kTailMaxN = 1024;          // components at which the tail takes over
+constexpr uint32_t kTailMaxPairs = kTailMaxN * (kTailMaxN - 1) / 2;
 
 // Phase kinds of the fused solve's phase log.
-enum : uint8_t { PH_START = 0, PH_INIT, PH_FIND0, PH_HOOK, PH_COMPRESS, PH_COMPACT, PH_EMIT };
+enum : uint8_t { PH_START = 0, PH_INIT, PH_FIND0, PH_HOOK, PH_COMPRESS, PH_COMPACT, PH_EMIT,
+                 PH_TAIL };
 
 __device__ __forceinline__ unsigned long long global_timer_ns()
 {
@@ -73,6 +76,8 @@ struct Ctl {
     uint32_t flag3[3];   // per-pass "chase unfinished" flags of the fused kernel
     uint32_t emitted;    // tree edges written by emit (own field: m_next may still be read)
     uint32_t status;  // ST_* bits
+    uint32_t tail_cnt[kMaxRounds + 2];  // tail edge-list lengths (fused schedule)
+    uint32_t tail_added;                // tree edges the tail added
     uint32_t nphase;  // entries used in the phase log (fused schedule)
     uint8_t phase_kind[kMaxPhaseLog];
     uint8_t phase_round[kMaxPhaseLog];
@@ -95,6 +100,10 @@ struct Ws {
     uint32_t *mst_bits;
     unsigned long long *desc;  // look-back descriptors
     uint32_t *bar;             // grid-barrier counters of the fused kernel
+    unsigned long long *pair_tab;  // lightest key per component pair (tail)
+    uint4 *tl[2];                  // tail edge lists (a, b, weight_bits, input id)
+    unsigned long long *tmin;      // tail: minimum key per component
+    int32_t *tpar;                 // tail: hook pointers
     uint32_t n_cap, m_cap, desc_cap;
 };
 
@@ -296,9 +305,14 @@ __device__ __forceinline__ unsigned long long desc_word(uint32_t epoch, unsigned
     return ((unsigned long long)(epoch & 0x7fffffffu) << 33) | flag | (value & 0x7fffffffu);
 }
 
-// Called by all 32 lanes of warp 0.  Publishes the tile's aggregate, looks
-// back over predecessors 32 at a time, publishes the inclusive prefix and
-// returns the exclusive prefix (same value in every lane).
+// Called by all 32 lanes of one warp.  Publishes the tile's aggregate, looks
+// back over predecessors 32*kLookPerLane at a time (lane l reads distances
+// l*kLookPerLane .. +kLookPerLane-1), publishes the inclusive prefix and
+// returns the exclusive prefix (same value in every lane).  Measured on
+// GB300: reading 4 per lane was slower than 1 (the extra loads cost more
+// than the shorter walks save), so one per lane it is.
+constexpr int kLookPerLane = 1;
+
 __device__ __forceinline__ uint32_t lookback_warp(unsigned long long *desc, uint32_t tile,
                                                   uint32_t aggregate, uint32_t epoch,
                                                   uint32_t *status)
@@ -316,43 +330,58 @@ __device__ __forceinline__ uint32_t lookback_warp(unsigned long long *desc, uint
     int64_t hi = (int64_t)tile - 1;  // nearest predecessor not yet summed
     uint32_t spins = 0;
     for (;;) {
-        const int64_t idx = hi - lane;
-        unsigned long long d;
-        uint32_t flag, val;
-        if (idx >= 0) {
-            d = ld_relaxed_u64(&desc[idx]);
-            flag = (d >> 33) == ep ? (uint32_t)((d >> 31) & 3u) : 0u;
-            val = (uint32_t)(d & 0x7fffffffu);
-        } else {
-            flag = 2u;  // before tile 0: prefix 0
-            val = 0u;
+        // this lane's 4 predecessors, nearest first: flag, value
+        uint32_t flag[kLookPerLane], val[kLookPerLane];
+#pragma unroll
+        for (int k = 0; k < kLookPerLane; k++) {
+            const int64_t idx = hi - (lane * kLookPerLane + k);
+            if (idx >= 0) {
+                const unsigned long long d = ld_relaxed_u64(&desc[idx]);
+                flag[k] = (d >> 33) == ep ? (uint32_t)((d >> 31) & 3u) : 0u;
+                val[k] = (uint32_t)(d & 0x7fffffffu);
+            } else {
+                flag[k] = 2u;  // before tile 0: prefix 0
+                val[k] = 0u;
+            }
         }
-        const uint32_t pmask = __ballot_sync(0xffffffffu, flag == 2u);
-        const uint32_t zmask = __ballot_sync(0xffffffffu, flag == 0u);
+        // within the lane: first prefix, any gap before it, sum up to it
+        int first = kLookPerLane;
+        bool gap = false;
+        uint32_t part = 0;
+#pragma unroll
+        for (int k = kLookPerLane - 1; k >= 0; k--)
+            if (flag[k] == 2u)
+                first = k;
+#pragma unroll
+        for (int k = 0; k < kLookPerLane; k++)
+            if (k <= first && k < kLookPerLane) {
+                gap |= flag[k] == 0u;
+                part += val[k];
+            }
+        const uint32_t pmask = __ballot_sync(0xffffffffu, first < kLookPerLane);
+        const uint32_t zmask = __ballot_sync(0xffffffffu, gap);
         const uint32_t stop = pmask ? (uint32_t)(__ffs(pmask) - 1) : 32u;
         const uint32_t need = stop == 32u ? 0xffffffffu : ((2u << stop) - 1u);
         if (zmask & need) {  // an unpublished tile before the nearest prefix: wait
             if (++spins > kSpinLimit) {
                 if (lane == 0) {
                     atomicOr(status, ST_TIMEOUT);
-                    const int z = __ffs(zmask & need) - 1;
-                    printf("mst: look-back gave up: tile %u epoch %u waiting on tile %lld "
-                           "(block %u of %u)\n", tile, epoch, (long long)(hi - z), blockIdx.x,
-                           gridDim.x);
+                    printf("mst: look-back gave up: tile %u epoch %u (block %u of %u)\n", tile,
+                           epoch, blockIdx.x, gridDim.x);
                 }
                 break;
             }
             __nanosleep(20);
             continue;
         }
-        uint32_t part = ((uint32_t)lane <= stop) ? val : 0u;
+        uint32_t sum = ((uint32_t)lane <= stop) ? part : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
-            part += __shfl_xor_sync(0xffffffffu, part, o);
-        excl += part;
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        excl += sum;
         if (stop != 32u)
             break;
-        hi -= 32;
+        hi -= 32 * kLookPerLane;
     }
     if (lane == 0)
         st_relaxed_u64(&desc[tile], desc_word(epoch, kDescPrefix, excl + aggregate));

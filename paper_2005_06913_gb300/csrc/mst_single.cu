@@ -436,23 +436,23 @@ __device__ __forceinline__ void finish(Ctl *c, int64_t *out_count, uint32_t emit
 // value it saw when it arrived.  One atomic per block, nothing to reset.
 // Waits are bounded: on expiry ST_TIMEOUT is set and later barriers no
 // longer wait.
-constexpr uint32_t kBarCount = 0, kBarGen = 32;  // kBarGen: unused slot kept for layout
+constexpr uint32_t kBarCount = 0;
 constexpr uint32_t kBarSpinLimit = 1u << 22;
 
-__device__ __forceinline__ void grid_sync(uint32_t *bar, uint32_t &gen, uint32_t *status)
+// Barrier among CTAs [0, nb) (all co-resident); `slot` picks the counter.
+__device__ __forceinline__ void team_sync(uint32_t *counter, uint32_t nb, uint32_t *status)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t nb = gridDim.x;
         const uint32_t inc = blockIdx.x == 0 ? 0x80000000u - (nb - 1) : 1u;
         __threadfence();
-        const uint32_t old = atomicAdd(bar + kBarCount, inc);
+        const uint32_t old = atomicAdd(counter, inc);
         uint32_t spins = 0;
-        while (((old ^ ld_volatile_u32(bar + kBarCount)) & 0x80000000u) == 0) {
+        while (((old ^ ld_volatile_u32(counter)) & 0x80000000u) == 0) {
             if (++spins > kBarSpinLimit) {
                 atomicOr(status, ST_TIMEOUT);
                 printf("mst: grid barrier gave up: block %u of %u, arrival value %u, now %u\n",
-                       blockIdx.x, nb, old, ld_volatile_u32(bar + kBarCount));
+                       blockIdx.x, nb, old, ld_volatile_u32(counter));
                 break;
             }
             if (ld_volatile_u32(status) & ST_TIMEOUT)
@@ -463,8 +463,15 @@ __device__ __forceinline__ void grid_sync(uint32_t *bar, uint32_t &gen, uint32_t
         __threadfence();
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void grid_sync(uint32_t *bar, uint32_t &gen, uint32_t *status)
+{
+    team_sync(bar + kBarCount, gridDim.x, status);
     gen++;
 }
+
+constexpr uint32_t kBarTeam = 32;  // counter of the tail's sub-grid team (own 128-B line)
 
 size_t bar_words(int) { return 64; }
 
@@ -491,6 +498,232 @@ __device__ __forceinline__ void log_phase(Ctl *c, uint8_t kind, uint32_t round =
             c->nphase = i + 1;
         }
     }
+}
+
+// ----------------------------------------------------------------- the tail
+//
+// Once a round leaves at most kTailMaxN components, that round's compaction
+// does not write a next edge list: every surviving edge offers its key
+// (weight_bits, input id) to a dense table with one slot per component pair
+// (a < b).  Of parallel edges between the same two components only the
+// lightest can be in the tree (a heavier one closes a cycle with it), so the
+// table's non-empty slots are the whole remaining problem.  They are
+// gathered into a short list and finished by Boruvka rounds in which each
+// edge checks whether it is the minimum of its endpoints (hook by edge), so
+// the list needs no order and survivors are appended with one atomic per
+// warp.  The list is finished by a team of CTAs sized to it (one CTA per
+// kTailEdgesPerCta edges): a single CTA uses block barriers and shared
+// memory, a larger team a barrier among its own CTAs.
+
+// Appends the lanes' kept records to `list` (one atomic per warp).
+__device__ __forceinline__ void warp_append(uint4 *list, uint32_t *counter, bool keep,
+                                            const uint4 &rec)
+{
+    const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (!mask)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader)
+        base = atomicAdd(counter, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (keep)
+        list[base + __popc(mask & lanemask_lt())] = rec;
+}
+
+// Tail-mode compaction of one warp tile: edges between different components
+// of round r+1 offer (weight_bits, input id) to their pair's slot.
+template <bool R0>
+__device__ __forceinline__ void compact_pairs_wtile(const Ws &ws, Ctl *c, uint32_t tile,
+                                                    uint32_t round, uint32_t m_cur,
+                                                    uint32_t n_next, uint32_t n_in, uint32_t wt,
+                                                    const int32_t *src, const int32_t *dst,
+                                                    const uint32_t *w)
+{
+    const int lane = threadIdx.x & 31;
+    const uint4 *ecur = (round & 1) ? ws.E[1] : ws.E[0];
+    const int32_t *__restrict__ lab = ws.lab;
+    uint32_t *status = &c->status;
+    const uint32_t base = tile * kCompWTile;
+#pragma unroll
+    for (int j = 0; j < kCompIpl; j++) {
+        const uint32_t i = base + j * 32 + lane;
+        if (i >= m_cur)
+            continue;
+        uint4 rec;
+        bool ok;
+        if (R0) {
+            rec = make_uint4((uint32_t)__ldg(src + i), (uint32_t)__ldg(dst + i), __ldg(w + i), i);
+            ok = rec.x < n_in && rec.y < n_in && rec.x != rec.y;
+        } else {
+            rec = ecur[i];
+            ok = true;
+        }
+        if (!ok)
+            continue;
+        const uint32_t nu = (uint32_t)lab[rec.x], nv = (uint32_t)lab[rec.y];
+        if (nu >= n_next || nv >= n_next) {
+            atomicOr(status, ST_INTERNAL);
+            continue;
+        }
+        if (nu == nv)
+            continue;
+        const uint32_t wb = R0 ? weight_bits(rec.z, wt, status) : rec.z;
+        const uint32_t a = nu < nv ? nu : nv, b = nu < nv ? nv : nu;
+        offer_min(&ws.pair_tab[(size_t)a * n_next + b], make_key(wb, rec.w));
+    }
+}
+
+// Gathers the non-empty pair slots into tail list 0 (grid-stride).
+__device__ __forceinline__ void extract_pairs(const Ws &ws, Ctl *c, uint32_t n_t, size_t i0,
+                                              size_t step)
+{
+    const size_t total = (size_t)n_t * n_t;
+    const size_t rounds = (total + step - 1) / step;  // every lane runs the same trip count
+    for (size_t k = 0; k < rounds; k++) {
+        const size_t i = i0 + k * step;
+        bool keep = false;
+        uint4 rec = make_uint4(0, 0, 0, 0);
+        if (i < total) {
+            const uint32_t a = (uint32_t)(i / n_t), b = (uint32_t)(i % n_t);
+            if (a < b) {
+                const unsigned long long key = ws.pair_tab[i];
+                if (key != kNoEdge) {
+                    keep = true;
+                    rec = make_uint4(a, b, (uint32_t)(key >> 32), (uint32_t)key);
+                }
+            }
+        }
+        warp_append(ws.tl[0], &c->tail_cnt[0], keep, rec);
+    }
+}
+
+// Boruvka rounds on the tail list by a team of CTAs [0, team): CTA 0 alone,
+// with the per-component arrays in its shared memory, or several CTAs (a
+// barrier among just them) with the arrays in global memory.  Component ids stay in
+// [0, n_t) (roots keep their ids, no renumbering).  Edge loops take kTailU
+// edges per thread per step so their loads overlap.  Returns the number of
+// components left.
+constexpr int kTailU = 4;
+constexpr uint32_t kTailEdgesPerCta = 2048;
+
+__device__ uint32_t tail_solve(const Ws &ws, Ctl *c, uint32_t n_t, uint32_t m_t, uint32_t r_base,
+                               uint32_t team, unsigned long long *tmin, int32_t *tpar_)
+{
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nthr = (size_t)team * blockDim.x;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    auto sync = [&]() {
+        if (team > 1)
+            team_sync(ws.bar + kBarTeam, team, &c->status);
+        else
+            __syncthreads();
+    };
+    volatile int32_t *tpar = tpar_;
+    volatile unsigned long long *vmin = tmin;
+    uint32_t cur = 0, comps = n_t;
+    for (uint32_t tr = 0; m_t > 0; tr++) {
+        if (tr >= (uint32_t)kMaxRounds) {
+            if (leader)
+                atomicOr(&c->status, ST_INTERNAL);
+            break;
+        }
+        const uint4 *L = ws.tl[cur];
+        uint4 *Ln = ws.tl[cur ^ 1];
+        for (size_t v = tid; v < n_t; v += nthr) {
+            tmin[v] = kNoEdge;
+            tpar[v] = (int32_t)v;
+        }
+        sync();
+        for (size_t e0 = tid; e0 < m_t; e0 += kTailU * nthr) {  // find-min
+            uint4 r[kTailU];
+#pragma unroll
+            for (int k = 0; k < kTailU; k++) {
+                const size_t e = e0 + k * nthr;
+                r[k] = e < m_t ? L[e] : make_uint4(0, 0, 0xffffffffu, 0xffffffffu);
+            }
+#pragma unroll
+            for (int k = 0; k < kTailU; k++) {
+                if (e0 + k * nthr >= m_t)
+                    continue;
+                const unsigned long long key = make_key(r[k].z, r[k].w);
+                if (key < vmin[r[k].x])
+                    atomicMin(&tmin[r[k].x], key);
+                if (key < vmin[r[k].y])
+                    atomicMin(&tmin[r[k].y], key);
+            }
+        }
+        sync();
+        for (size_t e0 = tid; e0 < m_t; e0 += kTailU * nthr) {  // hook by edge
+            uint4 r[kTailU];
+#pragma unroll
+            for (int k = 0; k < kTailU; k++) {
+                const size_t e = e0 + k * nthr;
+                r[k] = e < m_t ? L[e] : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < kTailU; k++) {
+                if (e0 + k * nthr >= m_t)
+                    continue;
+                const unsigned long long key = make_key(r[k].z, r[k].w);
+                const bool ha = vmin[r[k].x] == key, hb = vmin[r[k].y] == key;
+                if (!ha && !hb)
+                    continue;
+                const uint32_t a = r[k].x, b = r[k].y;
+                if (ha && hb)  // mutual: the lower id stays root
+                    tpar[a > b ? a : b] = (int32_t)(a < b ? a : b);
+                else if (ha)
+                    tpar[a] = (int32_t)b;
+                else
+                    tpar[b] = (int32_t)a;
+                red_or_u32(&ws.mst_bits[r[k].w >> 5], 1u << (r[k].w & 31));
+                atomicAdd(&c->tail_added, 1u);
+            }
+        }
+        sync();
+        for (size_t v = tid; v < n_t; v += nthr) {  // compress: chase with halving
+            uint32_t x = (uint32_t)v;
+            for (uint32_t hop = 0; hop <= n_t; hop++) {  // depth < n_t: always ends
+                const uint32_t p = (uint32_t)tpar[x];
+                if (p == x)
+                    break;
+                const uint32_t gp = (uint32_t)tpar[p];
+                tpar[x] = (int32_t)gp;
+                x = gp;
+            }
+        }
+        sync();
+        const size_t steps = (m_t + nthr - 1) / nthr;  // relabel + drop internal edges
+        for (size_t k = 0; k < steps; k++) {
+            const size_t e = tid + k * nthr;
+            bool keep = false;
+            uint4 r = make_uint4(0, 0, 0, 0);
+            if (e < m_t) {
+                r = L[e];
+                uint32_t a = r.x, b = r.y;
+                for (uint32_t hop = 0; hop <= n_t && (uint32_t)tpar[a] != a; hop++)
+                    a = (uint32_t)tpar[a];
+                for (uint32_t hop = 0; hop <= n_t && (uint32_t)tpar[b] != b; hop++)
+                    b = (uint32_t)tpar[b];
+                keep = a != b;
+                r.x = a;
+                r.y = b;
+            }
+            warp_append(Ln, &c->tail_cnt[tr + 1], keep, r);
+        }
+        sync();
+        m_t = ld_volatile_u32(&c->tail_cnt[tr + 1]);
+        comps = n_t - ld_volatile_u32(&c->tail_added);
+        if (leader && r_base + tr + 1 <= (uint32_t)kMaxRounds) {
+            c->stat_m[r_base + tr + 1] = m_t;
+            c->stat_n[r_base + tr + 1] = comps;
+        }
+        cur ^= 1;
+        if (team > 1 && (ld_volatile_u32(&c->status) & ST_TIMEOUT))
+            break;
+    }
+    return comps;
 }
 
 // ------------------------------------------------- fused persistent kernel
@@ -547,6 +780,11 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         grid_sync(ws.bar, gen, status);
         log_phase(c, PH_HOOK, r);
         const uint32_t n_next = nth ? ld_volatile_u32(&c->n_next) : 0u;
+        // few components left: this round's compaction feeds the tail instead
+        const bool tail = n_next >= 2 && n_next <= kTailMaxN && m_cur > 0;
+        if (tail)
+            for (size_t i = gtid; i < (size_t)n_next * n_next; i += gstride)
+                ws.pair_tab[i] = kNoEdge;
         // compress, with extra pointer-jumping passes while chains are deep
         for (uint32_t pass = 0;; pass++) {
             if (bid == 0 && threadIdx.x == 0)
@@ -564,6 +802,48 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
                     atomicOr(status, ST_INTERNAL);
                 break;
             }
+        }
+        if (tail) {
+            const uint32_t ntp = (m_cur + kCompWTile - 1) / kCompWTile;
+            for (uint32_t t = gw; t < ntp; t += nw) {
+                if (r == 0)
+                    compact_pairs_wtile<true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
+                else
+                    compact_pairs_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
+            }
+            mark_work(c);
+            grid_sync(ws.bar, gen, status);
+            log_phase(c, PH_COMPACT, r);
+            extract_pairs(ws, c, n_next, gtid, gstride);
+            mark_work(c);
+            grid_sync(ws.bar, gen, status);
+            const uint32_t m_t = ld_volatile_u32(&c->tail_cnt[0]);
+            if (gtid == 0 && r + 1 <= (uint32_t)kMaxRounds) {
+                c->stat_m[r + 1] = m_t;
+                c->stat_n[r + 1] = n_next;
+            }
+            // team size: one CTA per kTailEdgesPerCta edges of the list
+            uint32_t team = (m_t + kTailEdgesPerCta - 1) / kTailEdgesPerCta;
+            team = team < 1 ? 1 : (team > nb ? nb : team);
+            if (bid < team) {
+                if (team == 1) {  // per-component arrays in CTA 0's shared stage
+                    unsigned long long *smin = (unsigned long long *)sm.stage;
+                    int32_t *spar = (int32_t *)(smin + kTailMaxN);
+                    tail_solve(ws, c, n_next, m_t, r + 1, 1, smin, spar);
+                } else {
+                    tail_solve(ws, c, n_next, m_t, r + 1, team, ws.tmin, ws.tpar);
+                }
+            }
+            mark_work(c);
+            grid_sync(ws.bar, gen, status);
+            log_phase(c, PH_TAIL, r + 1);
+            // components left and rounds run, as CTA 0 recorded them
+            n_cur = n_next - ld_volatile_u32(&c->tail_added);
+            uint32_t tr = 0;
+            while (r + 1 + tr + 1 <= (uint32_t)kMaxRounds && ld_volatile_u32(&c->tail_cnt[tr]) > 0)
+                tr++;
+            r = r + tr;  // rounds finished by the tail
+            break;
         }
         // compact (+ find-min of the next round)
         const uint32_t ntc = (m_cur + kCompWTile - 1) / kCompWTile;
@@ -800,6 +1080,9 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += 3 * align_up((size_t)n_cap * 4);
     b += align_up((((size_t)m_cap + 31) / 32) * 4);
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 8);
+    b += align_up((size_t)kTailMaxN * kTailMaxN * 8);   // pair table
+    b += 2 * align_up((size_t)kTailMaxPairs * 16);      // tail lists
+    b += align_up((size_t)kTailMaxN * 8) + align_up((size_t)kTailMaxN * 4);
     return b;
 }
 
@@ -937,6 +1220,11 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.mst_bits = (uint32_t *)take((((size_t)m_cap + 31) / 32) * 4);
     s.ws.desc_cap = desc_capacity(n_cap, m_cap);
     s.ws.desc = (unsigned long long *)take((size_t)s.ws.desc_cap * 8);
+    s.ws.pair_tab = (unsigned long long *)take((size_t)kTailMaxN * kTailMaxN * 8);
+    s.ws.tl[0] = (uint4 *)take((size_t)kTailMaxPairs * 16);
+    s.ws.tl[1] = (uint4 *)take((size_t)kTailMaxPairs * 16);
+    s.ws.tmin = (unsigned long long *)take((size_t)kTailMaxN * 8);
+    s.ws.tpar = (int32_t *)take((size_t)kTailMaxN * 4);
     s.ws.n_cap = n_cap;
     s.ws.m_cap = m_cap;
     MST_TRY(cudaMemset(s.ws.ctl, 0, sizeof(Ctl)));
@@ -1105,7 +1393,8 @@ cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<Ker
     MST_TRY(cudaStreamSynchronize(stream));
     Ctl c;
     MST_TRY(cudaMemcpy(&c, s.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-    static const char *names[] = {"start", "init", "find0", "hook", "compress", "compact", "emit"};
+    static const char *names[] = {"start", "init", "find0", "hook",
+                                  "compress", "compact", "emit", "tail"};
     const double n = c.n, m = c.m;
     auto bytes_of = [&](int kind, uint32_t r) -> double {
         switch (kind) {
@@ -1133,7 +1422,7 @@ cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<Ker
     double wait_ms = 0.0;
     int waits = 0;
     for (uint32_t i = 1; i < np; i++) {
-        const int k = c.phase_kind[i] < 7 ? c.phase_kind[i] : 0;
+        const int k = c.phase_kind[i] < 8 ? c.phase_kind[i] : 0;
         const uint32_t r = c.phase_round[i];
         const double ms = (double)(c.phase_ns[i] - c.phase_ns[i - 1]) * 1e-6;
         double b = bytes_of(k, r < (uint32_t)kMaxRounds ? r : 0);

@@ -301,7 +301,12 @@ def test_fused_phase_log(handle):
         return sum(p["launches"] for p in prof if p["name"].startswith("k_solve:" + kind))
 
     assert count("find0") == 1 and count("emit") == 1 and count("init") == 1
-    assert count("hook") == rounds == count("compact")
-    assert count("compress") >= rounds
+    # grid rounds have a hook, compress and compaction phase each; once few
+    # components remain, one tail phase finishes the remaining rounds
+    assert count("hook") == count("compact") <= rounds
+    assert count("compress") >= count("hook")
+    assert count("tail") <= 1
+    if count("tail") == 0:
+        assert count("hook") == rounds
     assert all(p["total_ms"] > 0 for p in prof)
     B.mst_set_single_schedule(handle, 0, 0)

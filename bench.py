@@ -536,6 +536,7 @@ def run_serving(args):
         picks = rng.integers(0, pool.G, arrivals.shape[0])
         tickets, lat, done_t = {}, [], []
         slot_busy = {}
+        errors = 0
         t_start = time.perf_counter()
         k = 0
         while k < arrivals.shape[0] or tickets:
@@ -555,6 +556,7 @@ def run_serving(args):
             for t in list(tickets):
                 st, dn, l_us = B.mst_poll(h, t)
                 if dn:
+                    errors += int(st != B.MST_OK)
                     slot, n_g = tickets.pop(t)
                     slot_busy.pop(slot, None)
                     lat.append(l_us * 1e-3)
@@ -564,7 +566,7 @@ def run_serving(args):
         B.mst_server_stop(h)
         B.mst_destroy(h)
         p50, p99 = _percentiles(lat)
-        results.append({"rate_offered": rate, "requests": len(lat),
+        results.append({"rate_offered": rate, "requests": len(lat), "errors": errors,
                         "graphs_per_s": len(lat) / elapsed, "latency_ms": {"p50": p50, "p99": p99}})
     # one solve at a time on one stream, same pool, back to back (its best case)
     h = B.mst_create(0, 0)

@@ -88,6 +88,13 @@ mst_status mst_destroy(mst_handle h);
  *                 (n - number of connected components).
  * Runs asynchronously on `stream`.  Returns MST_ERR_INVALID_ARG for negative
  * or too-large sizes, NULL pointers with nonzero sizes, or a NULL handle.
+ * Under the default (fused) schedule the solve is one cooperative launch
+ * whose CTAs wait on each other at grid barriers.  Two such solves running
+ * at the same time on one device (other streams or handles) can each be
+ * left partly resident; their barriers then give up after a bounded wait
+ * and the solve reports MST_ERR_TIMEOUT.  Order fused solves on one device
+ * (one stream, or events), or use the graph schedule for concurrent ones;
+ * batched solves and other kernels may run beside a fused solve.
  */
 mst_status mst_solve(mst_handle h, int32_t n, int64_t m,
                      const int32_t *src, const int32_t *dst, const void *w,
@@ -241,7 +248,10 @@ mst_status mst_solve_noalloc(mst_weight_type wt, int32_t n, int64_t m,
  * admitted group as one batched solve on one of `streams` CUDA streams, and
  * admits new requests as soon as a stream and memory are free, so solves of
  * requests that arrive while others run overlap on the GPU.  max_batch caps
- * the graphs per launch.
+ * the graphs per launch.  A request with more than 131072 edges is not
+ * batched: it is solved alone by the fused single-graph kernel (half the
+ * persistent grid) in a workspace owned by its stream, one such request at a
+ * time, while small requests keep being batched past it on other streams.
  */
 mst_status mst_server_start(mst_handle h, int streams, int max_batch);
 

@@ -10,6 +10,10 @@
 // latency is completion minus submit time) and the memory is released.  So
 // requests that arrive while other batches run on the GPU are admitted as
 // soon as a slot and memory free up, and their solves overlap on the device.
+// Large requests (more than kServeBigM edges) are not batched: one CTA per
+// graph would take tens of milliseconds on them.  A slot solves such a
+// request alone with the fused multi-CTA single-graph kernel in its own
+// workspace, while other slots keep serving batches.
 // Each request's result is the same as a solve of that graph alone: the
 // minimum spanning tree under the (weight, edge id) order is unique.
 #include <cuda_runtime.h>
@@ -23,7 +27,12 @@
 
 namespace mst {
 
+constexpr int64_t kServeBigM = 131072;  // larger requests get the fused kernel
+constexpr int kServeFusedCtasPerSm = 2;  // leaves room for batches on other slots
+
 struct Slot {
+    Single single;                // fused-kernel workspace for large requests
+    bool big = false;             // the request in flight is a large one
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     GraphDesc *h_desc = nullptr;  // pinned host descriptors
@@ -54,6 +63,7 @@ struct Server {
     uint64_t next_ticket = 1;
     size_t in_use = 0;
     int inflight = 0;
+    bool big_inflight = false;  // a fused single-graph solve is running
     bool stop = false;
     cudaError_t error = cudaSuccess;
 };
@@ -68,8 +78,12 @@ static void complete_slot(Server &S, Slot &sl)
 {
     const double t = now_us();
     uint32_t bits = 0;
-    cudaMemcpy(&bits, sl.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost);
-    cudaFreeAsync(sl.ws, sl.stream);
+    if (sl.big) {
+        cudaMemcpy(&bits, &sl.single.ws.ctl->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    } else {
+        cudaMemcpy(&bits, sl.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        cudaFreeAsync(sl.ws, sl.stream);
+    }
     const mst_status st = status_from_bits(bits & ~(uint32_t)ST_DISCONNECTED);
     std::lock_guard<std::mutex> lk(S.mu);
     for (uint64_t tk : sl.tickets) {
@@ -79,39 +93,103 @@ static void complete_slot(Server &S, Slot &sl)
         o.status = st;
         S.submit_us.erase(tk);
     }
-    S.in_use -= sl.ws_bytes;
+    if (!sl.big)
+        S.in_use -= sl.ws_bytes;
+    else
+        S.big_inflight = false;
     S.inflight--;
     sl.tickets.clear();
     sl.ws = nullptr;
     sl.ws_bytes = 0;
+    sl.big = false;
     sl.busy = false;
     S.cv.notify_all();
 }
 
-// Takes queued requests for one batch (lock held).  Requests that can never
-// fit the budget are completed at once with MST_ERR_BUDGET.
-static std::vector<Request> take_batch(Server &S, size_t budget)
+// Takes queued requests for one launch (lock held).  Large requests form
+// their own FIFO lane with at most one in flight: the fused kernel's grid
+// barrier needs all of its CTAs resident at once, and two fused grids that
+// are each partly resident would wait on each other until the barrier gives
+// up.  One fused grid next to batched kernels (which never wait on anything)
+// always completes.  Small requests are batched in arrival order, passing
+// large ones that wait for the lane.  Requests that can never fit the budget
+// are completed at once with MST_ERR_BUDGET.
+static void reject(Server &S, std::deque<Request>::iterator it)
+{
+    Outcome &o = S.results[it->ticket];
+    o.done = true;
+    o.status = MST_ERR_BUDGET;
+    S.submit_us.erase(it->ticket);
+}
+
+static std::vector<Request> take_batch(Server &S, Slot &sl, size_t budget, bool *big)
 {
     std::vector<Request> batch;
+    *big = false;
+    if (!S.big_inflight) {
+        for (auto it = S.pending.begin(); it != S.pending.end();) {
+            if (it->m <= kServeBigM) {
+                ++it;
+                continue;
+            }
+            const size_t have = sl.single.base ? sl.single.bytes : 0;
+            const size_t need = single_bytes((uint32_t)std::max<int64_t>(it->n, 1024),
+                                             (uint32_t)std::max<int64_t>(it->m, 1024));
+            if (budget && need > budget) {  // can never be admitted
+                reject(S, it);
+                it = S.pending.erase(it);
+                continue;
+            }
+            if (budget && need > have && S.in_use - have + need > budget)
+                break;  // wait for memory; small requests may still go
+            batch.push_back(*it);
+            S.pending.erase(it);
+            *big = true;
+            return batch;
+        }
+    }
     size_t bytes = 4096 + 64 * 4;  // control block and order list slack
-    while (!S.pending.empty() && (int)batch.size() < S.max_batch) {
-        Request &r = S.pending.front();
-        const size_t need = request_bytes((uint32_t)r.n, (uint32_t)r.m);
+    for (auto it = S.pending.begin(); it != S.pending.end() && (int)batch.size() < S.max_batch;) {
+        if (it->m > kServeBigM) {
+            ++it;
+            continue;
+        }
+        const size_t need = request_bytes((uint32_t)it->n, (uint32_t)it->m);
         if (budget && need + 4096 > budget) {  // can never be admitted
-            Outcome &o = S.results[r.ticket];
-            o.done = true;
-            o.status = MST_ERR_BUDGET;
-            S.submit_us.erase(r.ticket);
-            S.pending.pop_front();
+            reject(S, it);
+            it = S.pending.erase(it);
             continue;
         }
         if (budget && S.in_use + bytes + need > budget)
             break;
         bytes += need;
-        batch.push_back(r);
-        S.pending.pop_front();
+        batch.push_back(*it);
+        it = S.pending.erase(it);
     }
     return batch;
+}
+
+// A large request on the slot's fused-kernel workspace (grown if needed).
+static cudaError_t launch_big(Server &S, Slot &sl, const Request &r)
+{
+    const uint32_t n = (uint32_t)r.n, m = (uint32_t)r.m;
+    if (!sl.single.base || n > sl.single.ws.n_cap || m > sl.single.ws.m_cap) {
+        const size_t before = sl.single.base ? sl.single.bytes : 0;
+        sl.single.fused_blocks_per_sm = kServeFusedCtasPerSm;
+        cudaError_t e = single_reserve(sl.single, S.h->device, n, m);
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.in_use = S.in_use - before + (sl.single.base ? sl.single.bytes : 0);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (n == 0)
+        return cudaMemsetAsync(r.out_count, 0, sizeof(int64_t), sl.stream);
+    cudaError_t e = single_launch(sl.single, r.src, r.dst, r.w, r.wt, r.out, r.out_count, n, m,
+                                  sl.stream);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(sl.done, sl.stream);
+    sl.tickets.assign(1, r.ticket);
+    return e;
 }
 
 static cudaError_t launch_batch(Server &S, Slot &sl, std::vector<Request> &batch)
@@ -184,8 +262,9 @@ static void server_loop(Server *Sp)
                 break;
             }
         std::vector<Request> batch;
+        bool big = false;
         if (free_slot && !S.pending.empty())
-            batch = take_batch(S, budget);
+            batch = take_batch(S, *free_slot, budget, &big);
         if (batch.empty()) {
             S.cv.notify_all();
             // nothing to launch: wait for a submit or poll the busy slots soon
@@ -193,13 +272,17 @@ static void server_loop(Server *Sp)
             continue;
         }
         size_t bytes = 0;
-        for (const Request &r : batch)
-            bytes += request_bytes((uint32_t)r.n, (uint32_t)r.m);
-        S.in_use += bytes + 4096;
+        if (!big)
+            for (const Request &r : batch)
+                bytes += request_bytes((uint32_t)r.n, (uint32_t)r.m);
+        if (!big)
+            S.in_use += bytes + 4096;
         S.inflight++;
+        S.big_inflight |= big;
         free_slot->busy = true;
+        free_slot->big = big;
         lk.unlock();
-        cudaError_t e = launch_batch(S, *free_slot, batch);
+        cudaError_t e = big ? launch_big(S, *free_slot, batch[0]) : launch_batch(S, *free_slot, batch);
         if (e != cudaSuccess) {
             cudaGetLastError();
             std::lock_guard<std::mutex> g(S.mu);
@@ -209,15 +292,19 @@ static void server_loop(Server *Sp)
                 o.done = true;
                 o.status = e == cudaErrorMemoryAllocation ? MST_ERR_OOM : MST_ERR_CUDA;
             }
-            S.in_use -= bytes + 4096;
+            if (!big)
+                S.in_use -= bytes + 4096;
+            else
+                S.big_inflight = false;
             S.inflight--;
             free_slot->busy = false;
+            free_slot->big = false;
             free_slot->tickets.clear();
             if (free_slot->ws) {
                 cudaFreeAsync(free_slot->ws, free_slot->stream);
                 free_slot->ws = nullptr;
             }
-        } else {
+        } else if (!big) {
             free_slot->ws_bytes = bytes + 4096;  // the admission charge
         }
     }
@@ -315,6 +402,7 @@ mst_status server_stop(mst_handle h)
             cudaFreeHost(sl.h_desc);
         if (sl.d_desc)
             cudaFree(sl.d_desc);
+        single_release(sl.single);
     }
     const mst_status st = S->error == cudaSuccess ? MST_OK : MST_ERR_CUDA;
     delete S;

@@ -108,3 +108,36 @@ def test_server_lifecycle_errors(lib_built):
         assert B.mst_server_stop(h) == B.MST_ERR_INVALID_ARG
     finally:
         B.mst_destroy(h)
+
+
+def test_serving_large_requests_use_fused_path(lib_built):
+    """Requests above the batching threshold are solved alone by the fused
+    multi-CTA kernel on a slot while other slots serve batches: two large ones
+    back to back (both slots fused at once), a larger one after a smaller one
+    (the slot's workspace grows), a disconnected large one (a forest)."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    small = [gg.random_connected(500 + 300 * i, 3000 + 900 * i, 40 + i, weights="f32")
+             for i in range(10)]
+    big1 = gg.random_connected(60000, 180000, 7, weights="f32")
+    big2 = gg.grid2d(400, 400, 8)
+    big3 = gg.random_connected(150000, 450000, 9, weights="f32")
+    a = gg.random_connected(50000, 150000, 10)
+    b = gg.random_connected(30000, 90000, 11)
+    forest = gg.Graph(a.n + b.n, np.r_[a.src, b.src + a.n].astype(np.int32),
+                      np.r_[a.dst, b.dst + a.n].astype(np.int32), np.r_[a.w, b.w], "two parts")
+    graphs = small[:3] + [big1, big2] + small[3:6] + [big3] + small[6:8] + [forest] + small[8:]
+    h = B.mst_create(0, 0)
+    try:
+        assert B.mst_server_start(h, 2, 8) == B.MST_OK
+        reqs = submit_all(h, graphs)
+        res = wait_all(h, reqs)
+        assert B.mst_server_drain(h) == B.MST_OK
+        for t, g, out, cnt, _ in reqs:
+            st, lat = res[t]
+            assert st == B.MST_OK and lat > 0, g.name
+            got = out[: int(cnt.item())].cpu().numpy().astype(np.int64)
+            assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w)), g.name
+    finally:
+        B.mst_server_stop(h)
+        B.mst_destroy(h)

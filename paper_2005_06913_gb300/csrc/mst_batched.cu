@@ -433,7 +433,7 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
     for (uint32_t i = t; i < words; i += T)
         A.bits[i] = 0u;
     tm.sync();
-    // round-0 find-min (Section 2.1 steps 15-28)
+    // round-0 find-min (Section 2.1, the loop over edges)
     for (uint32_t e = t; e < m; e += T) {
         const uint32_t u = (uint32_t)__ldg(src + e), v = (uint32_t)__ldg(dst + e);
         if (u >= n || v >= n) {
@@ -450,7 +450,7 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
     uint32_t n_r = n, m_r = m;
     unsigned long long *mc = A.mA, *mx = A.mB;
     for (uint32_t r = 0;; r++) {
-        // hook (steps 30-40) and dense renumbering of roots, warp tiles
+        // hook (Section 2.1, the union step) and dense renumbering of roots, warp tiles
         const int lane = threadIdx.x & 31;
         const uint32_t lt = lanemask_lt();
         uint32_t run = 0;

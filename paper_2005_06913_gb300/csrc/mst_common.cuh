@@ -2,13 +2,14 @@
 // and batched Boruvka solvers: the control block, the workspace layout, the
 // edge key, ballot-based tile ranking and the decoupled look-back scan.
 //
-// Edge key (Section 2.1, steps 21 and 24 compare weights; ties are broken by
-// edge position): key = (weight_bits << 32) | position.  weight_bits is the
+// Edge key (Section 2.1: the find-min loop compares weights; ties are
+// broken by edge id): key = (weight_bits << 32) | tag.  weight_bits is the
 // uint32 weight, or for float32 an order-preserving remap of the IEEE bits.
-// position is the edge's index in the live edge list of the current round;
-// every compaction is stable, so position order equals input edge-id order
-// among the edges that are still alive, and min over keys is min over
-// (weight, edge id).
+// The single-graph solver tags with the input edge id itself and finds the
+// edge's record through a position-by-id map.  The batched solver tags with
+// the edge's index in its live list; its compaction is stable, so position
+// order equals edge-id order among the edges still alive.  Either way the
+// minimum over keys is the minimum over (weight, edge id).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -76,6 +77,8 @@ struct Ctl {
     uint32_t flag3[3];   // per-pass "chase unfinished" flags of the fused kernel
     uint32_t emitted;    // tree edges written by emit (own field: m_next may still be read)
     uint32_t status;  // ST_* bits
+    uint32_t cnt_n[kMaxRounds + 2];  // roots numbered so far in round r (hook)
+    uint32_t cnt_m[kMaxRounds + 2];  // edges kept so far in round r (compaction)
     uint32_t tail_cnt[kMaxRounds + 2];  // tail edge-list lengths (fused schedule)
     uint32_t tail_added;                // tree edges the tail added
     uint32_t nphase;  // entries used in the phase log (fused schedule)
@@ -98,7 +101,8 @@ struct Ws {
     int32_t *nid;      // new dense id of each root
     int32_t *lab;      // new id of each component after compression
     uint32_t *mst_bits;
-    unsigned long long *desc;  // look-back descriptors
+    uint32_t *epos;            // position of each live edge in the current list, by input id
+    unsigned long long *desc;  // look-back descriptors (emit)
     uint32_t *bar;             // grid-barrier counters of the fused kernel
     unsigned long long *pair_tab;  // lightest key per component pair (tail)
     uint4 *tl[2];                  // tail edge lists (a, b, weight_bits, input id)

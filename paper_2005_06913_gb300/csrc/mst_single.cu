@@ -4,29 +4,33 @@
 // Round r works on a contracted graph: components are numbered 0..n_r-1 and
 // the live edge list holds only edges between different components, with
 // endpoints already renamed to component ids.  Per round:
-//   find-min (Section 2.1 steps 15-28): every live edge offers its key to
-//     both endpoint components with a 64-bit atomicMin (the key packs the
-//     weight above the edge's list position, so ties break by edge id);
-//     for round r+1 this runs fused into round r's compaction.
-//   hook (steps 30-40): every component c with a minimum edge e to d points
-//     at d and marks e as a tree edge, except that of two components that
-//     chose the same edge the lower id stays a root.  Under a total order
-//     that mutual pair is the only cycle the pointers can form, so they form
-//     a forest (the lock/CAS serialisation of Sections 2.2.1-2.2.2 is not
-//     needed).  Roots get new dense ids by a prefix sum.
+//   find-min (Section 2.1, the loop over edges): every live edge offers its
+//     key to both endpoint components with a 64-bit atomicMin (the key packs
+//     the weight above the input edge id, so ties break by edge id); for
+//     round r+1 this runs fused into round r's compaction.
+//   hook (Section 2.1, the union step): every component c with a minimum
+//     edge e to d points at d and marks e as a tree edge, except that of two
+//     components that chose the same edge the lower id stays a root.  Under
+//     a total order that mutual pair is the only cycle the pointers can
+//     form, so they form a forest (the lock/CAS serialisation of Sections
+//     2.2.1-2.2.2 is not needed).  Roots get new dense ids: each warp tile
+//     takes a block of ids with one atomicAdd (the numbering is arbitrary;
+//     the tree does not depend on it).
 //   compress: each component follows its pointers to its root (path halving,
 //     bounded hops per pass, more passes only while some chain is deep) and
 //     takes the root's new id.
 //   compact (Section 2.1 "Optimization", covered edges): edges whose two
-//     renamed endpoints coincide are dropped; survivors are written, in their
-//     old order, to the next list, and offer their keys for round r+1.
+//     renamed endpoints coincide are dropped; each warp tile writes its
+//     survivors to a block of positions taken with one atomicAdd, records
+//     each survivor's position under its input id, and offers its keys for
+//     round r+1.
 // The rounds stop when no live edge is left; the tree edges are then emitted
 // in ascending id order.
 //
 // Two schedules run the same tile bodies:
 //   fused  (default) one cooperative persistent launch, k_solve, walks every
-//          phase of every round; phases are separated by a two-level grid
-//          barrier instead of kernel boundaries.
+//          phase of every round; phases are separated by a grid barrier
+//          instead of kernel boundaries.
 //   graph  one kernel per phase, captured once into a CUDA graph whose round
 //          loop and pointer-jump loop are device-controlled conditional WHILE
 //          nodes (k_init, k_find0, k_hook, k_compress, k_compact, k_emit).
@@ -136,12 +140,14 @@ constexpr uint32_t kGroupedMaxComponents = 0u;  // measured: grouping costs more
 
 constexpr int kHookWTile = 32 * kHookIpl, kCompWTile = 32 * kCompIpl;
 
-// Hook one warp tile of components (Section 2.1 steps 30-40) and give the
-// tile's roots dense new ids.  The warp owning the last tile stores n_next.
+// Hook one warp tile of components (Section 2.1, the union step) and give
+// the tile's roots new ids from the round's counter.  The minimum key's tag
+// is the input edge id: round 0 reads the input endpoints, later rounds the
+// edge's record at its recorded position.
 template <bool R0>
-__device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, uint32_t ntiles,
-                                           uint32_t round, uint32_t epoch, uint32_t n_cur,
-                                           const int32_t *src, const int32_t *dst)
+__device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, uint32_t round,
+                                           uint32_t n_cur, const int32_t *src,
+                                           const int32_t *dst)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long *mcur = (round & 1) ? ws.mins[1] : ws.mins[0];
@@ -169,10 +175,10 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
                 b[j] = (uint32_t)__ldg(dst + p);
                 id[j] = p;
             } else {
-                const uint4 r = ecur[p];
+                const uint4 r = ecur[__ldcg(ws.epos + p)];
                 a[j] = r.x;
                 b[j] = r.y;
-                id[j] = r.w;
+                id[j] = p;
             }
         }
     }
@@ -202,9 +208,10 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
         mask[j] = __ballot_sync(0xffffffffu, root);
         total += __popc(mask[j]);
     }
-    const uint32_t ex = lookback_warp(ws.desc, tile, total, epoch, &c->status);
-    if (lane == 0 && tile == ntiles - 1)
-        c->n_next = ex + total;
+    uint32_t ex = 0;
+    if (lane == 0 && total)
+        ex = atomicAdd(&c->cnt_n[round], total);
+    ex = __shfl_sync(0xffffffffu, ex, 0);
     const uint32_t lt = lanemask_lt();
     uint32_t run = ex;
 #pragma unroll
@@ -268,14 +275,14 @@ __device__ __forceinline__ bool compress_range(const Ws &ws, uint32_t n_cur, boo
 }
 
 // Compaction of one warp tile of round r's live edges fused with find-min
-// of round r+1: survivors are written from registers to consecutive
-// positions (one contiguous run per row of the tile) and offer their keys
-// with fire-and-forget reductions.  The warp owning the last tile stores
-// m_next.
+// of round r+1: survivors are written from registers to a block of
+// positions taken from the round's counter (one contiguous run per row of
+// the tile), their positions are recorded by input id, and they offer their
+// (weight, id) keys with fire-and-forget reductions.
 template <bool R0>
 __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t tile,
-                                              uint32_t ntiles, uint32_t round, uint32_t epoch,
-                                              uint32_t m_cur, uint32_t n_next, uint32_t n_in,
+                                              uint32_t round, uint32_t m_cur, uint32_t n_next,
+                                              uint32_t n_in,
                                               uint32_t wt, const int32_t *src, const int32_t *dst,
                                               const uint32_t *w)
 {
@@ -322,9 +329,10 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
         mask[j] = __ballot_sync(0xffffffffu, keep);
         total += __popc(mask[j]);
     }
-    const uint32_t ex = lookback_warp(ws.desc, tile, total, epoch, status);
-    if (lane == 0 && tile == ntiles - 1)
-        c->m_next = ex + total;
+    uint32_t ex = 0;
+    if (lane == 0 && total)
+        ex = atomicAdd(&c->cnt_m[round], total);
+    ex = __shfl_sync(0xffffffffu, ex, 0);
     const uint32_t lt = lanemask_lt();
     // few components left: many lanes of a warp offer to the same one
     const bool grouped = n_next <= kGroupedMaxComponents;
@@ -335,7 +343,8 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
         if ((mask[j] >> lane) & 1u) {
             const uint32_t pos = run + __popc(mask[j] & lt);
             enext[pos] = rec[j];
-            const unsigned long long key = make_key(rec[j].z, pos);
+            __stcg(ws.epos + rec[j].w, pos);
+            const unsigned long long key = make_key(rec[j].z, rec[j].w);
             if (grouped) {
                 offer_min_grouped(mnext, mask[j], rec[j].x, key);
                 offer_min_grouped(mnext, mask[j], rec[j].y, key);
@@ -771,15 +780,14 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             c->flag3[0] = 0;
         for (uint32_t t = gw; t < nth; t += nw) {
             if (r == 0)
-                hook_wtile<true>(ws, c, t, nth, r, ep, n_cur, src, dst);
+                hook_wtile<true>(ws, c, t, r, n_cur, src, dst);
             else
-                hook_wtile<false>(ws, c, t, nth, r, ep, n_cur, src, dst);
+                hook_wtile<false>(ws, c, t, r, n_cur, src, dst);
         }
-        ep++;
         mark_work(c);
         grid_sync(ws.bar, gen, status);
         log_phase(c, PH_HOOK, r);
-        const uint32_t n_next = nth ? ld_volatile_u32(&c->n_next) : 0u;
+        const uint32_t n_next = ld_volatile_u32(&c->cnt_n[r]);
         // few components left: this round's compaction feeds the tail instead
         const bool tail = n_next >= 2 && n_next <= kTailMaxN && m_cur > 0;
         if (tail)
@@ -849,15 +857,14 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         const uint32_t ntc = (m_cur + kCompWTile - 1) / kCompWTile;
         for (uint32_t t = gw; t < ntc; t += nw) {
             if (r == 0)
-                compact_wtile<true>(ws, c, t, ntc, r, ep, m_cur, n_next, n, wt, src, dst, w);
+                compact_wtile<true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
             else
-                compact_wtile<false>(ws, c, t, ntc, r, ep, m_cur, n_next, n, wt, src, dst, w);
+                compact_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
         }
-        ep++;
         mark_work(c);
         grid_sync(ws.bar, gen, status);
         log_phase(c, PH_COMPACT, r);
-        const uint32_t m_next = ntc ? ld_volatile_u32(&c->m_next) : 0u;
+        const uint32_t m_next = ld_volatile_u32(&c->cnt_m[r]);
         if (gtid == 0 && r + 1 <= (uint32_t)kMaxRounds) {
             c->stat_m[r + 1] = m_next;
             c->stat_n[r + 1] = n_next;
@@ -950,18 +957,16 @@ __global__ void __launch_bounds__(kThreads) k_hook(Ws ws)
 {
     __shared__ uint32_t s_flag;
     Ctl *c = ws.ctl;
-    const uint32_t round = c->round, epoch = c->epoch, n_cur = c->n_cur;
+    const uint32_t round = c->round, n_cur = c->n_cur;
     const uint32_t ntiles = (n_cur + kHookWTile - 1) / kHookWTile;
     for (;;) {
         const uint32_t tile = next_warp_tile(&c->ticket);
         if (tile >= ntiles)
             break;
-        hook_wtile<R0>(ws, c, tile, ntiles, round, epoch, n_cur, c->src, c->dst);
+        hook_wtile<R0>(ws, c, tile, round, n_cur, c->src, c->dst);
     }
     if (last_block_done(&c->done, &s_flag) && threadIdx.x == 0) {
-        if (ntiles == 0)
-            c->n_next = 0;
-        c->epoch = epoch + 1;
+        c->n_next = ld_volatile_u32(&c->cnt_n[round]);
         c->ticket = 0;
         c->done = 0;
     }
@@ -1001,17 +1006,18 @@ k_compact(Ws ws, cudaGraphConditionalHandle loop, uint32_t graph_mode)
 {
     __shared__ uint32_t s_flag;
     Ctl *c = ws.ctl;
-    const uint32_t round = c->round, epoch = c->epoch, m_cur = c->m_cur, n_next = c->n_next;
+    const uint32_t round = c->round, m_cur = c->m_cur, n_next = c->n_next;
     const uint32_t ntiles = (m_cur + kCompWTile - 1) / kCompWTile;
     for (;;) {
         const uint32_t tile = next_warp_tile(&c->ticket);
         if (tile >= ntiles)
             break;
-        compact_wtile<R0>(ws, c, tile, ntiles, round, epoch, m_cur, n_next, c->n, c->wt, c->src,
-                          c->dst, (const uint32_t *)c->w);
+        compact_wtile<R0>(ws, c, tile, round, m_cur, n_next, c->n, c->wt, c->src, c->dst,
+                          (const uint32_t *)c->w);
     }
     if (last_block_done(&c->done, &s_flag) && threadIdx.x == 0) {
-        const uint32_t m_next = ntiles ? ld_volatile_u32(&c->m_next) : 0u;
+        const uint32_t m_next = ld_volatile_u32(&c->cnt_m[round]);
+        c->m_next = m_next;
         const uint32_t r1 = round + 1;
         if (r1 <= (uint32_t)kMaxRounds) {
             c->stat_m[r1] = m_next;
@@ -1020,7 +1026,6 @@ k_compact(Ws ws, cudaGraphConditionalHandle loop, uint32_t graph_mode)
         c->m_cur = m_next;
         c->n_cur = n_next;
         c->round = r1;
-        c->epoch = epoch + 1;
         c->ticket = 0;
         c->done = 0;
         bool more = m_next > 0;
@@ -1062,11 +1067,9 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static uint32_t desc_capacity(uint32_t n_cap, uint32_t m_cap)
 {
+    (void)n_cap;  // only emit scans with look-back
     const uint32_t words = (m_cap + 31) / 32;
-    uint32_t t = (m_cap + kCompWTile - 1) / kCompWTile;
-    t = t > (n_cap + kHookWTile - 1) / kHookWTile ? t : (n_cap + kHookWTile - 1) / kHookWTile;
-    t = t > (words + kEmitWords - 1) / kEmitWords ? t : (words + kEmitWords - 1) / kEmitWords;
-    return t + 1;
+    return (words + kEmitWords - 1) / kEmitWords + 1;
 }
 
 static const int kMaxGridBlocks = 152 * 8 * 2;  // bound for the barrier counters
@@ -1079,6 +1082,7 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += 2 * align_up((size_t)n_cap * 8);
     b += 3 * align_up((size_t)n_cap * 4);
     b += align_up((((size_t)m_cap + 31) / 32) * 4);
+    b += align_up((size_t)m_cap * 4);  // edge positions by id
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 8);
     b += align_up((size_t)kTailMaxN * kTailMaxN * 8);   // pair table
     b += 2 * align_up((size_t)kTailMaxPairs * 16);      // tail lists
@@ -1218,6 +1222,7 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.nid = (int32_t *)take((size_t)n_cap * 4);
     s.ws.lab = (int32_t *)take((size_t)n_cap * 4);
     s.ws.mst_bits = (uint32_t *)take((((size_t)m_cap + 31) / 32) * 4);
+    s.ws.epos = (uint32_t *)take((size_t)m_cap * 4);
     s.ws.desc_cap = desc_capacity(n_cap, m_cap);
     s.ws.desc = (unsigned long long *)take((size_t)s.ws.desc_cap * 8);
     s.ws.pair_tab = (unsigned long long *)take((size_t)kTailMaxN * kTailMaxN * 8);

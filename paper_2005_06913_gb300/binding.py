@@ -48,7 +48,7 @@ _SIGS = {
     "mst_get_status": (_INT, [_P, _P]),
     "mst_get_round_stats": (_INT, [_P, _P, _P, _P, _I32, ctypes.POINTER(_I32)]),
     "mst_set_batched_schedule": (_INT, [_P, _INT, _INT]),
-    "mst_set_single_schedule": (_INT, [_P, _INT, _INT]),
+    "mst_set_single_schedule": (_INT, [_P, _INT, _INT, _INT]),
     "mst_autotune_batched": (_INT, [_P, _INT, _I32, _P, _P, _I64, _I64, _P, _P, _P, _P, _P,
                                     ctypes.c_char_p, _P]),
     "mst_solve_noalloc": (_INT, [_INT, _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
@@ -182,8 +182,8 @@ def mst_get_round_stats(h, stream=None, cap: int = 65):
     return list(e[:k]), list(v[:k])
 
 
-def mst_set_single_schedule(h, schedule: int, blocks_per_sm: int = 0) -> int:
-    return lib().mst_set_single_schedule(h, int(schedule), int(blocks_per_sm))
+def mst_set_single_schedule(h, schedule: int, blocks_per_sm: int = 0, block_threads: int = 0) -> int:
+    return lib().mst_set_single_schedule(h, int(schedule), int(blocks_per_sm), int(block_threads))
 
 
 def mst_set_batched_schedule(h, schedule: int, block_threads: int = 0) -> int:

@@ -346,16 +346,22 @@ mst_status mst_set_batched_schedule(mst_handle h, int schedule, int block_thread
     return MST_OK;
 }
 
-mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm)
+mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm,
+                                   int block_threads)
 {
-    if (!h || schedule < 0 || schedule > 2 || blocks_per_sm < 0 || blocks_per_sm > 8)
+    if (!h || schedule < 0 || schedule > 2 || blocks_per_sm < 0 || blocks_per_sm > 8 ||
+        (block_threads != 0 && block_threads != 256 && block_threads != 512 &&
+         block_threads != 768 && block_threads != 1024))
         return MST_ERR_INVALID_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess)
         return MST_ERR_CUDA;
     cudaDeviceSynchronize();
     h->single.schedule = schedule;
-    if (blocks_per_sm > 0 && blocks_per_sm != h->single.fused_blocks_per_sm) {
-        h->single.fused_blocks_per_sm = blocks_per_sm;
+    const int bps = blocks_per_sm > 0 ? blocks_per_sm : h->single.fused_blocks_per_sm;
+    const int ft = block_threads > 0 ? block_threads : h->single.fused_threads;
+    if (bps != h->single.fused_blocks_per_sm || ft != h->single.fused_threads) {
+        h->single.fused_blocks_per_sm = bps;
+        h->single.fused_threads = ft;
         single_release(h->single);  // the grid is fixed at reservation time
         h->last_solve.valid = false;
     }

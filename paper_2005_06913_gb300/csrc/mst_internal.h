@@ -31,7 +31,8 @@ struct Single {
     int grid_tiles = 0;     // persistent grid of the tile kernels
     int grid_stream = 0;    // grid of the grid-stride kernels
     int grid_fused = 0;     // co-resident grid of the fused cooperative kernel
-    int fused_blocks_per_sm = 4;
+    int fused_blocks_per_sm = 4;  // CTAs per SM of the fused kernel (clamped by occupancy)
+    int fused_threads = 256;      // threads per CTA of the fused kernel
     int schedule = 0;       // 0/1 fused cooperative kernel, 2 CUDA graph of kernels
     uint64_t solves = 0;    // solves since the descriptors were last cleared
 };

@@ -28,7 +28,7 @@
 namespace mst {
 
 constexpr int64_t kServeBigM = 131072;  // larger requests get the fused kernel
-constexpr int kServeFusedCtasPerSm = 2;  // leaves room for batches on other slots
+constexpr int kServeFusedThreads = 512;  // one such CTA per SM leaves room for batches
 
 struct Slot {
     Single single;                // fused-kernel workspace for large requests
@@ -175,7 +175,8 @@ static cudaError_t launch_big(Server &S, Slot &sl, const Request &r)
     const uint32_t n = (uint32_t)r.n, m = (uint32_t)r.m;
     if (!sl.single.base || n > sl.single.ws.n_cap || m > sl.single.ws.m_cap) {
         const size_t before = sl.single.base ? sl.single.bytes : 0;
-        sl.single.fused_blocks_per_sm = kServeFusedCtasPerSm;
+        sl.single.fused_blocks_per_sm = 1;
+        sl.single.fused_threads = kServeFusedThreads;
         cudaError_t e = single_reserve(sl.single, S.h->device, n, m);
         std::lock_guard<std::mutex> lk(S.mu);
         S.in_use = S.in_use - before + (sl.single.base ? sl.single.bytes : 0);

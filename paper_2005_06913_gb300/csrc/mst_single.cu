@@ -222,53 +222,91 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
     }
 }
 
-// Follows hook pointers from `start` with path halving, at most kChaseLimit
-// steps.  Returns true and the root when it gets there.
-__device__ __forceinline__ bool chase(int32_t *parent, uint32_t start, uint32_t &at)
-{
-    uint32_t x = start;
-#pragma unroll 1
-    for (int s = 0; s < kChaseLimit; s++) {
-        const uint32_t p = (uint32_t)__ldcg(parent + x);
-        if (p == x) {
-            at = x;
-            return true;
-        }
-        const uint32_t gp = (uint32_t)__ldcg(parent + p);
-        if (gp == p) {
-            at = p;
-            return true;
-        }
-        __stcg(parent + x, (int32_t)gp);
-        x = gp;
-    }
-    at = x;
-    return false;
-}
+// One compress pass over components [v0, n_cur) step vstep: each thread
+// follows the hook pointers of kCompressU components in lock step (path
+// halving, at most kChaseLimit steps), so their loads overlap, and gives
+// each the new id of its root; a component whose chase did not end keeps
+// lab = -1 and its pointer moved up the chain for the next pass.  Pointer
+// loads may come from L1: every value a pointer has held in this pass is an
+// ancestor, so an older one only shortens the step.
+constexpr int kCompressU = 2;
 
-// lab[v] = new id of v's root, for v in [v0, n_cur) step vstep.  A follow-up
-// pass (first == false) only revisits components whose chase did not end.
-// Returns true if some chase in this thread did not end.
 __device__ __forceinline__ bool compress_range(const Ws &ws, uint32_t n_cur, bool first,
                                                size_t v0, size_t vstep)
 {
     int32_t *parent = ws.parent;
     bool unfinished = false;
-    for (size_t vi = v0; vi < n_cur; vi += vstep) {
-        const uint32_t v = (uint32_t)vi;
-        uint32_t start = v;
-        if (!first) {
-            if (__ldcg(ws.lab + v) != -1)
-                continue;
-            start = (uint32_t)__ldcg(parent + v);
+    for (size_t b0 = v0; b0 < n_cur; b0 += kCompressU * vstep) {
+        uint32_t x[kCompressU];
+        bool act[kCompressU];
+#pragma unroll
+        for (int i = 0; i < kCompressU; i++) {
+            const size_t v = b0 + i * vstep;
+            act[i] = v < n_cur;
+            x[i] = (uint32_t)v;
         }
-        uint32_t at;
-        if (chase(parent, start, at)) {
-            ws.lab[v] = ws.nid[at];
-        } else {
-            ws.lab[v] = -1;
-            __stcg(parent + v, (int32_t)at);
-            unfinished = true;
+        if (!first) {  // follow-up pass: only components left unfinished
+#pragma unroll
+            for (int i = 0; i < kCompressU; i++)
+                act[i] = act[i] && __ldcg(ws.lab + x[i]) == -1;
+#pragma unroll
+            for (int i = 0; i < kCompressU; i++)
+                x[i] = act[i] ? (uint32_t)__ldcg(parent + x[i]) : x[i];
+        }
+        uint32_t root[kCompressU];
+        bool done[kCompressU];
+#pragma unroll
+        for (int i = 0; i < kCompressU; i++) {
+            done[i] = !act[i];
+            root[i] = 0;
+        }
+#pragma unroll 1
+        for (int s = 0; s < kChaseLimit; s++) {
+            uint32_t p[kCompressU], gp[kCompressU];
+#pragma unroll
+            for (int i = 0; i < kCompressU; i++)
+                p[i] = done[i] ? 0u : (uint32_t)__ldca(parent + x[i]);
+#pragma unroll
+            for (int i = 0; i < kCompressU; i++) {
+                if (!done[i] && p[i] == x[i]) {
+                    root[i] = x[i];
+                    done[i] = true;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kCompressU; i++)
+                gp[i] = done[i] ? 0u : (uint32_t)__ldca(parent + p[i]);
+            bool more = false;
+#pragma unroll
+            for (int i = 0; i < kCompressU; i++) {
+                if (done[i])
+                    continue;
+                if (gp[i] == p[i]) {
+                    root[i] = p[i];
+                    done[i] = true;
+                } else {
+                    __stcg(parent + x[i], (int32_t)gp[i]);
+                    x[i] = gp[i];
+                    more = true;
+                }
+            }
+            if (!more)
+                break;
+        }
+        int32_t nl[kCompressU];
+#pragma unroll
+        for (int i = 0; i < kCompressU; i++)
+            nl[i] = act[i] && done[i] ? __ldca(ws.nid + root[i]) : -1;
+#pragma unroll
+        for (int i = 0; i < kCompressU; i++) {
+            if (!act[i])
+                continue;
+            const uint32_t v = (uint32_t)(b0 + i * vstep);
+            ws.lab[v] = nl[i];
+            if (!done[i]) {
+                __stcg(parent + v, (int32_t)x[i]);
+                unfinished = true;
+            }
         }
     }
     return unfinished;
@@ -382,8 +420,9 @@ __device__ __forceinline__ void emit_tile(const Ws &ws, Ctl *c, uint32_t tile, u
     if (lane == 31)
         sm.s32[warp] = incl;
     __syncthreads();
+    const int nwarps = (int)(blockDim.x >> 5);
     if (warp == 0) {
-        const uint32_t v = lane < kWarps ? sm.s32[lane] : 0u;
+        const uint32_t v = lane < nwarps ? sm.s32[lane] : 0u;
         uint32_t inc2 = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -391,7 +430,7 @@ __device__ __forceinline__ void emit_tile(const Ws &ws, Ctl *c, uint32_t tile, u
             if (lane >= o)
                 inc2 += y;
         }
-        if (lane < kWarps)
+        if (lane < nwarps)
             sm.s32[lane] = inc2 - v;
         if (lane == 31)
             sm.s32[32] = inc2;
@@ -416,7 +455,7 @@ __device__ __forceinline__ void emit_tile(const Ws &ws, Ctl *c, uint32_t tile, u
     }
     __syncthreads();
     const uint32_t ex = sm.s_excl;
-    for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
+    for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
         if (ex + k < cap)
             out[ex + k] = (int32_t)ids[k];
         else
@@ -615,7 +654,7 @@ __device__ __forceinline__ void extract_pairs(const Ws &ws, Ctl *c, uint32_t n_t
 // edges per thread per step so their loads overlap.  Returns the number of
 // components left.
 constexpr int kTailU = 4;
-constexpr uint32_t kTailEdgesPerCta = 2048;
+constexpr uint32_t kTailEdgesPerThread = 8;
 
 __device__ uint32_t tail_solve(const Ws &ws, Ctl *c, uint32_t n_t, uint32_t m_t, uint32_t r_base,
                                uint32_t team, unsigned long long *tmin, int32_t *tpar_)
@@ -737,19 +776,24 @@ __device__ uint32_t tail_solve(const Ws &ws, Ctl *c, uint32_t n_t, uint32_t m_t,
 
 // ------------------------------------------------- fused persistent kernel
 
-// The whole solve in one cooperative launch.  Tiles are assigned statically
-// (tile t to block t mod grid, in increasing order), so every look-back wait
-// is on a tile whose block is resident and makes progress.
-__global__ void __launch_bounds__(kThreads, 4)
+// The whole solve in one cooperative launch of kFT-thread CTAs (64
+// registers a thread at any size: 256 x 4, 512 x 2 or 1024 x 1 per SM).
+// Tiles are assigned statically (warp tile t to global warp t mod warps, emit
+// tile t to CTA t mod grid, in increasing order), so every look-back wait of
+// emit is on a tile whose CTA is resident and makes progress.  Larger CTAs
+// make fewer arrivals at each grid barrier.
+template <int kFT>
+__global__ void __launch_bounds__(kFT, 1024 / kFT)
 k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_t *out,
         int64_t *out_count, uint32_t n, uint32_t m, uint32_t wt, uint32_t vec)
 {
+    constexpr int kFW = kFT / 32;
     __shared__ TileSmem sm;
     Ctl *c = ws.ctl;
     uint32_t *status = &c->status;
     const uint32_t nb = gridDim.x, bid = blockIdx.x;
-    const size_t gtid = (size_t)bid * kThreads + threadIdx.x, gstride = (size_t)nb * kThreads;
-    const uint32_t gw = bid * kWarps + (threadIdx.x >> 5), nw = nb * kWarps;  // global warp
+    const size_t gtid = (size_t)bid * kFT + threadIdx.x, gstride = (size_t)nb * kFT;
+    const uint32_t gw = bid * kFW + (threadIdx.x >> 5), nw = nb * kFW;  // global warp
     uint32_t gen = 0;  // barrier count (the barrier itself keeps no generation)
     uint32_t ep = c->epoch;
     log_phase(c, PH_START);
@@ -830,8 +874,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
                 c->stat_m[r + 1] = m_t;
                 c->stat_n[r + 1] = n_next;
             }
-            // team size: one CTA per kTailEdgesPerCta edges of the list
-            uint32_t team = (m_t + kTailEdgesPerCta - 1) / kTailEdgesPerCta;
+            // team size: one CTA per kTailEdgesPerThread edges a thread
+            constexpr uint32_t kPerCta = kTailEdgesPerThread * kFT;
+            uint32_t team = (m_t + kPerCta - 1) / kPerCta;
             team = team < 1 ? 1 : (team > nb ? nb : team);
             if (bid < team) {
                 if (team == 1) {  // per-component arrays in CTA 0's shared stage
@@ -1098,10 +1143,11 @@ void single_release(Single &s)
         cudaGraphDestroy(s.graph);
     if (s.base)
         cudaFree(s.base);
-    const int schedule = s.schedule, bps = s.fused_blocks_per_sm;
+    const int schedule = s.schedule, bps = s.fused_blocks_per_sm, ft = s.fused_threads;
     s = Single();
     s.schedule = schedule;
     s.fused_blocks_per_sm = bps;
+    s.fused_threads = ft;
 }
 
 #define MST_TRY(x)                     \
@@ -1183,13 +1229,24 @@ static cudaError_t build_graph(Single &s)
     return cudaSuccess;
 }
 
-static int occupancy(const void *func, size_t smem)
+static int occupancy(const void *func, size_t smem, int threads = kThreads)
 {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, func, kThreads, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, func, threads, smem) != cudaSuccess ||
         blocks < 1)
         blocks = 1;
     return blocks;
+}
+
+// The fused kernel for a CTA size (256, 512, 768 or 1024 threads).
+static const void *fused_kernel(int threads)
+{
+    switch (threads) {
+    case 256: return (const void *)k_solve<256>;
+    case 512: return (const void *)k_solve<512>;
+    case 768: return (const void *)k_solve<768>;
+    default: return (const void *)k_solve<1024>;
+    }
 }
 
 cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
@@ -1243,7 +1300,7 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     occ = occ > 4 ? 4 : occ;
     s.grid_tiles = sms * occ;
     s.grid_stream = sms * 4;
-    int occ_f = occupancy((const void *)k_solve, 0);
+    int occ_f = occupancy(fused_kernel(s.fused_threads), 0, s.fused_threads);
     occ_f = occ_f > s.fused_blocks_per_sm ? s.fused_blocks_per_sm : occ_f;
     s.grid_fused = sms * occ_f;
     if (s.grid_fused > kMaxGridBlocks)
@@ -1278,8 +1335,8 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
         const uint32_t *wp = (const uint32_t *)w;
         void *args[] = {(void *)&s.ws, (void *)&src, (void *)&dst, (void *)&wp, (void *)&out,
                         (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec};
-        return cudaLaunchCooperativeKernel((const void *)k_solve, dim3(s.grid_fused),
-                                           dim3(kThreads), args, 0, stream);
+        return cudaLaunchCooperativeKernel(fused_kernel(s.fused_threads), dim3(s.grid_fused),
+                                           dim3(s.fused_threads), args, 0, stream);
     }
     k_init<<<s.grid_stream, kThreads, 0, stream>>>(s.ws, src, dst, w, out, out_count, n, m, wt,
                                                    vec);

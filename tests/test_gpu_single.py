@@ -56,14 +56,22 @@ def test_random_connected(sched, n, m):
     check(sched, g.n, g.src, g.dst, g.w)
 
 
-@pytest.mark.parametrize("bps", [1, 2, 8])
-def test_fused_grid_sizes(handle, bps):
-    assert B.mst_set_single_schedule(handle, 1, bps) == B.MST_OK
+@pytest.mark.parametrize("bps,threads", [(1, 1024), (1, 256), (4, 256), (8, 256), (2, 512),
+                                         (1, 768), (4, 1024)])
+def test_fused_grid_sizes(handle, bps, threads):
+    """Every CTA size and CTAs-per-SM setting (clamped to what fits) gives
+    the same tree, on a graph that reaches the tail and one that does not."""
+    assert B.mst_set_single_schedule(handle, 1, bps, threads) == B.MST_OK
     try:
-        g = gg.random_connected(30000, 90001, 5 + bps)
-        check(handle, g.n, g.src, g.dst, g.w)
+        for g in (gg.random_connected(30000, 90001, 5 + bps), gg.grid2d(200, 300, threads)):
+            check(handle, g.n, g.src, g.dst, g.w)
     finally:
-        B.mst_set_single_schedule(handle, 0, 4)
+        B.mst_set_single_schedule(handle, 0, 4, 256)
+
+
+def test_schedule_arg_errors(handle):
+    for bad in [(3, 0, 0), (-1, 0, 0), (1, 9, 0), (1, -1, 0), (1, 0, 100), (1, 0, 2048)]:
+        assert B.mst_set_single_schedule(handle, *bad) == B.MST_ERR_INVALID_ARG
 
 
 def test_config1(handle):

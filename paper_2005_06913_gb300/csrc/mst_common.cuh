@@ -80,6 +80,7 @@ struct Ctl {
     uint32_t cnt_n[kMaxRounds + 2];  // roots numbered so far in round r (hook)
     uint32_t cnt_m[kMaxRounds + 2];  // edges kept so far in round r (compaction)
     uint32_t tail_cnt[kMaxRounds + 2];  // tail edge-list lengths (fused schedule)
+    uint32_t tail_nn[kMaxRounds + 2];   // components after each tail round
     uint32_t tail_added;                // tree edges the tail added
     uint32_t nphase;  // entries used in the phase log (fused schedule)
     uint8_t phase_kind[kMaxPhaseLog];
@@ -107,7 +108,9 @@ struct Ws {
     unsigned long long *pair_tab;  // lightest key per component pair (tail)
     uint4 *tl[2];                  // tail edge lists (a, b, weight_bits, input id)
     unsigned long long *tmin;      // tail: minimum key per component
-    int32_t *tpar;                 // tail: hook pointers
+    int32_t *tpar;                 // tail: hook pointers, then roots
+    int32_t *tnid;                 // tail: new ids of the roots
+    uint32_t *ttouch;              // tail: pair slots written in a round
     uint32_t n_cap, m_cap, desc_cap;
 };
 

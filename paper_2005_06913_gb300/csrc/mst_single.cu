@@ -555,13 +555,21 @@ __device__ __forceinline__ void log_phase(Ctl *c, uint8_t kind, uint32_t round =
 // (weight_bits, input id) to a dense table with one slot per component pair
 // (a < b).  Of parallel edges between the same two components only the
 // lightest can be in the tree (a heavier one closes a cycle with it), so the
-// table's non-empty slots are the whole remaining problem.  They are
-// gathered into a short list and finished by Boruvka rounds in which each
-// edge checks whether it is the minimum of its endpoints (hook by edge), so
-// the list needs no order and survivors are appended with one atomic per
-// warp.  The list is finished by a team of CTAs sized to it (one CTA per
-// kTailEdgesPerCta edges): a single CTA uses block barriers and shared
-// memory, a larger team a barrier among its own CTAs.
+// table's non-empty slots are the whole remaining problem.  They become a
+// short list, and each tail round then runs on it:
+//   hook by edge: an edge that is the minimum of an endpoint hooks it (the
+//     list needs no order: the key names the edge);
+//   roots: every component finds its root; roots take dense new ids;
+//   merge: each edge between two different new components offers its key to
+//     the slot of that pair, and the first writer of a slot records it;
+//   next list: the recorded slots, read and reset, are the next round's list
+//     and offer their keys to their components (the next find-min).
+// So parallel edges are merged every round and a round costs O(list), not
+// O(table).  The rounds run on a team of CTAs sized to the list (one CTA per
+// kTailEdgesPerThread edges a thread, never growing): a team of one keeps
+// the per-component arrays in shared memory and syncs with block barriers,
+// a larger team keeps them in global memory and syncs with a barrier among
+// its own CTAs.
 
 // Appends the lanes' kept records to `list` (one atomic per warp).
 __device__ __forceinline__ void warp_append(uint4 *list, uint32_t *counter, bool keep,
@@ -580,6 +588,23 @@ __device__ __forceinline__ void warp_append(uint4 *list, uint32_t *counter, bool
         list[base + __popc(mask & lanemask_lt())] = rec;
 }
 
+// Appends the lanes' kept words to `list` (one atomic per warp).
+__device__ __forceinline__ void warp_append_u32(uint32_t *list, uint32_t *counter, bool keep,
+                                                uint32_t x)
+{
+    const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (!mask)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader)
+        base = atomicAdd(counter, (uint32_t)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (keep)
+        list[base + __popc(mask & lanemask_lt())] = x;
+}
+
 // Tail-mode compaction of one warp tile: edges between different components
 // of round r+1 offer (weight_bits, input id) to their pair's slot.
 template <bool R0>
@@ -591,7 +616,7 @@ __device__ __forceinline__ void compact_pairs_wtile(const Ws &ws, Ctl *c, uint32
 {
     const int lane = threadIdx.x & 31;
     const uint4 *ecur = (round & 1) ? ws.E[1] : ws.E[0];
-    const int32_t *__restrict__ lab = ws.lab;
+    const int32_t *lab = ws.lab;
     uint32_t *status = &c->status;
     const uint32_t base = tile * kCompWTile;
 #pragma unroll
@@ -623,7 +648,9 @@ __device__ __forceinline__ void compact_pairs_wtile(const Ws &ws, Ctl *c, uint32
     }
 }
 
-// Gathers the non-empty pair slots into tail list 0 (grid-stride).
+// Gathers the non-empty pair slots into tail list 0 (grid-stride), resets
+// them, and offers each pair's key to both of its components (find-min of
+// the first tail round).
 __device__ __forceinline__ void extract_pairs(const Ws &ws, Ctl *c, uint32_t n_t, size_t i0,
                                               size_t step)
 {
@@ -636,10 +663,13 @@ __device__ __forceinline__ void extract_pairs(const Ws &ws, Ctl *c, uint32_t n_t
         if (i < total) {
             const uint32_t a = (uint32_t)(i / n_t), b = (uint32_t)(i % n_t);
             if (a < b) {
-                const unsigned long long key = ws.pair_tab[i];
+                const unsigned long long key = __ldcg(ws.pair_tab + i);
                 if (key != kNoEdge) {
                     keep = true;
                     rec = make_uint4(a, b, (uint32_t)(key >> 32), (uint32_t)key);
+                    ws.pair_tab[i] = kNoEdge;
+                    offer_min(&ws.tmin[a], key);
+                    offer_min(&ws.tmin[b], key);
                 }
             }
         }
@@ -647,78 +677,78 @@ __device__ __forceinline__ void extract_pairs(const Ws &ws, Ctl *c, uint32_t n_t
     }
 }
 
-// Boruvka rounds on the tail list by a team of CTAs [0, team): CTA 0 alone,
-// with the per-component arrays in its shared memory, or several CTAs (a
-// barrier among just them) with the arrays in global memory.  Component ids stay in
-// [0, n_t) (roots keep their ids, no renumbering).  Edge loops take kTailU
-// edges per thread per step so their loads overlap.  Returns the number of
-// components left.
+// The tail rounds on list 0 (m_r pairs among n_r components, whose minimum
+// keys are already in ws.tmin and whose hook pointers are the identity).
+// Every CTA of the grid enters; CTAs outside a round's team leave.  CTA 0
+// always stays and records the components left in c->tail_added.
 constexpr int kTailU = 4;
 constexpr uint32_t kTailEdgesPerThread = 8;
 
-__device__ uint32_t tail_solve(const Ws &ws, Ctl *c, uint32_t n_t, uint32_t m_t, uint32_t r_base,
-                               uint32_t team, unsigned long long *tmin, int32_t *tpar_)
+template <int kFT>
+__device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, uint32_t r_base,
+                            TileSmem &sm)
 {
-    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t nthr = (size_t)team * blockDim.x;
-    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-    auto sync = [&]() {
-        if (team > 1)
-            team_sync(ws.bar + kBarTeam, team, &c->status);
-        else
-            __syncthreads();
-    };
-    volatile int32_t *tpar = tpar_;
-    volatile unsigned long long *vmin = tmin;
-    uint32_t cur = 0, comps = n_t;
-    for (uint32_t tr = 0; m_t > 0; tr++) {
-        if (tr >= (uint32_t)kMaxRounds) {
-            if (leader)
+    const uint32_t bid = blockIdx.x;
+    const uint32_t n_t = n_r;
+    uint32_t team_prev = gridDim.x;
+    volatile unsigned long long *tmin = ws.tmin;
+    volatile int32_t *tpar = ws.tpar;
+    volatile int32_t *tnid = ws.tnid;
+    bool local = false;  // per-component arrays in shared memory (team of one)
+    uint32_t cur = 0;
+    for (uint32_t tr = 0; m_r > 0; tr++) {
+        if (tr + 1 >= (uint32_t)kMaxRounds) {
+            if (bid == 0 && threadIdx.x == 0)
                 atomicOr(&c->status, ST_INTERNAL);
             break;
         }
+        constexpr uint32_t kPer = kTailEdgesPerThread * kFT;
+        uint32_t team = (m_r + kPer - 1) / kPer;
+        team = team < 1 ? 1 : (team > team_prev ? team_prev : team);
+        if (bid >= team)
+            return;
+        if (team == 1 && !local) {  // CTA 0 goes on alone: arrays into shared memory
+            unsigned long long *smin = (unsigned long long *)sm.stage;
+            int32_t *spar = (int32_t *)(smin + kTailMaxN);
+            int32_t *snid = spar + kTailMaxN;
+            for (uint32_t v = threadIdx.x; v < n_r; v += kFT) {
+                smin[v] = __ldcg(ws.tmin + v);
+                spar[v] = (int32_t)v;
+            }
+            __syncthreads();
+            tmin = smin;
+            tpar = spar;
+            tnid = snid;
+            local = true;
+        }
+        team_prev = team;
+        auto sync = [&]() {
+            if (team > 1)
+                team_sync(ws.bar + kBarTeam, team, &c->status);
+            else
+                __syncthreads();
+        };
+        const size_t tid = (size_t)bid * kFT + threadIdx.x;
+        const size_t nthr = (size_t)team * kFT;
         const uint4 *L = ws.tl[cur];
         uint4 *Ln = ws.tl[cur ^ 1];
-        for (size_t v = tid; v < n_t; v += nthr) {
-            tmin[v] = kNoEdge;
-            tpar[v] = (int32_t)v;
-        }
-        sync();
-        for (size_t e0 = tid; e0 < m_t; e0 += kTailU * nthr) {  // find-min
+        // hook by edge
+        for (size_t e0 = tid; e0 < m_r; e0 += kTailU * nthr) {
             uint4 r[kTailU];
 #pragma unroll
             for (int k = 0; k < kTailU; k++) {
                 const size_t e = e0 + k * nthr;
-                r[k] = e < m_t ? L[e] : make_uint4(0, 0, 0xffffffffu, 0xffffffffu);
+                r[k] = e < m_r ? __ldcg(L + e) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int k = 0; k < kTailU; k++) {
-                if (e0 + k * nthr >= m_t)
+                if (e0 + k * nthr >= m_r)
                     continue;
                 const unsigned long long key = make_key(r[k].z, r[k].w);
-                if (key < vmin[r[k].x])
-                    atomicMin(&tmin[r[k].x], key);
-                if (key < vmin[r[k].y])
-                    atomicMin(&tmin[r[k].y], key);
-            }
-        }
-        sync();
-        for (size_t e0 = tid; e0 < m_t; e0 += kTailU * nthr) {  // hook by edge
-            uint4 r[kTailU];
-#pragma unroll
-            for (int k = 0; k < kTailU; k++) {
-                const size_t e = e0 + k * nthr;
-                r[k] = e < m_t ? L[e] : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int k = 0; k < kTailU; k++) {
-                if (e0 + k * nthr >= m_t)
-                    continue;
-                const unsigned long long key = make_key(r[k].z, r[k].w);
-                const bool ha = vmin[r[k].x] == key, hb = vmin[r[k].y] == key;
+                const uint32_t a = r[k].x, b = r[k].y;
+                const bool ha = tmin[a] == key, hb = tmin[b] == key;
                 if (!ha && !hb)
                     continue;
-                const uint32_t a = r[k].x, b = r[k].y;
                 if (ha && hb)  // mutual: the lower id stays root
                     tpar[a > b ? a : b] = (int32_t)(a < b ? a : b);
                 else if (ha)
@@ -726,52 +756,80 @@ __device__ uint32_t tail_solve(const Ws &ws, Ctl *c, uint32_t n_t, uint32_t m_t,
                 else
                     tpar[b] = (int32_t)a;
                 red_or_u32(&ws.mst_bits[r[k].w >> 5], 1u << (r[k].w & 31));
-                atomicAdd(&c->tail_added, 1u);
             }
         }
         sync();
-        for (size_t v = tid; v < n_t; v += nthr) {  // compress: chase with halving
+        // roots: full path compression (any pointer value read is an
+        // ancestor); roots take dense new ids
+        uint32_t *nn = &c->tail_nn[tr];
+        for (size_t v = tid; v < n_r; v += nthr) {
             uint32_t x = (uint32_t)v;
-            for (uint32_t hop = 0; hop <= n_t; hop++) {  // depth < n_t: always ends
+            for (uint32_t hop = 0; hop < n_r; hop++) {  // a forest: depth < n_r
                 const uint32_t p = (uint32_t)tpar[x];
                 if (p == x)
                     break;
-                const uint32_t gp = (uint32_t)tpar[p];
-                tpar[x] = (int32_t)gp;
-                x = gp;
+                x = p;
             }
+            if (x == (uint32_t)v)
+                tnid[v] = (int32_t)atomicAdd(nn, 1u);
+            else
+                tpar[v] = (int32_t)x;
         }
         sync();
-        const size_t steps = (m_t + nthr - 1) / nthr;  // relabel + drop internal edges
+        const uint32_t n_next = ld_volatile_u32(nn);
+        // merge: relabel, offer to the pair slot; first writers record slots
+        uint32_t *touched = &c->tail_cnt[tr + 1];
+        const size_t steps = (m_r + nthr - 1) / nthr;  // every lane runs the same trip count
         for (size_t k = 0; k < steps; k++) {
             const size_t e = tid + k * nthr;
-            bool keep = false;
-            uint4 r = make_uint4(0, 0, 0, 0);
-            if (e < m_t) {
-                r = L[e];
-                uint32_t a = r.x, b = r.y;
-                for (uint32_t hop = 0; hop <= n_t && (uint32_t)tpar[a] != a; hop++)
-                    a = (uint32_t)tpar[a];
-                for (uint32_t hop = 0; hop <= n_t && (uint32_t)tpar[b] != b; hop++)
-                    b = (uint32_t)tpar[b];
-                keep = a != b;
-                r.x = a;
-                r.y = b;
+            bool first = false;
+            uint32_t slot = 0;
+            if (e < m_r) {
+                const uint4 r = __ldcg(L + e);
+                const uint32_t A = (uint32_t)tnid[tpar[r.x]], B = (uint32_t)tnid[tpar[r.y]];
+                if (A != B) {
+                    slot = (A < B ? A : B) * n_next + (A < B ? B : A);
+                    const unsigned long long key = make_key(r.z, r.w);
+                    if (key < __ldcg(ws.pair_tab + slot))
+                        first = atomicMin(ws.pair_tab + slot, key) == kNoEdge;
+                }
             }
-            warp_append(Ln, &c->tail_cnt[tr + 1], keep, r);
+            warp_append_u32(ws.ttouch, touched, first, slot);
         }
+        for (size_t v = tid; v < n_next; v += nthr)
+            tmin[v] = kNoEdge;
         sync();
-        m_t = ld_volatile_u32(&c->tail_cnt[tr + 1]);
-        comps = n_t - ld_volatile_u32(&c->tail_added);
-        if (leader && r_base + tr + 1 <= (uint32_t)kMaxRounds) {
-            c->stat_m[r_base + tr + 1] = m_t;
-            c->stat_n[r_base + tr + 1] = comps;
+        // next list: the recorded slots, reset; find-min of the next round
+        const uint32_t m_next = ld_volatile_u32(touched);
+        for (size_t i = tid; i < m_next; i += nthr) {
+            const uint32_t slot = __ldcg(ws.ttouch + i);
+            const unsigned long long key = __ldcg(ws.pair_tab + slot);
+            ws.pair_tab[slot] = kNoEdge;
+            const uint32_t a = slot / n_next, b = slot % n_next;
+            Ln[i] = make_uint4(a, b, (uint32_t)(key >> 32), (uint32_t)key);
+            if (local) {
+                atomicMin((unsigned long long *)&tmin[a], key);
+                atomicMin((unsigned long long *)&tmin[b], key);
+            } else {
+                offer_min(ws.tmin + a, key);
+                offer_min(ws.tmin + b, key);
+            }
         }
+        for (size_t v = tid; v < n_next; v += nthr)
+            tpar[v] = (int32_t)v;
+        sync();
+        if (bid == 0 && threadIdx.x == 0 && r_base + tr + 1 <= (uint32_t)kMaxRounds) {
+            c->stat_m[r_base + tr + 1] = m_next;
+            c->stat_n[r_base + tr + 1] = n_next;
+        }
+        m_r = m_next;
+        n_r = n_next;
         cur ^= 1;
         if (team > 1 && (ld_volatile_u32(&c->status) & ST_TIMEOUT))
             break;
     }
-    return comps;
+    if (bid == 0 && threadIdx.x == 0)
+        c->tail_added = n_t - n_r;
 }
 
 // ------------------------------------------------- fused persistent kernel
@@ -834,9 +892,14 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         const uint32_t n_next = ld_volatile_u32(&c->cnt_n[r]);
         // few components left: this round's compaction feeds the tail instead
         const bool tail = n_next >= 2 && n_next <= kTailMaxN && m_cur > 0;
-        if (tail)
+        if (tail) {
             for (size_t i = gtid; i < (size_t)n_next * n_next; i += gstride)
                 ws.pair_tab[i] = kNoEdge;
+            for (size_t v = gtid; v < n_next; v += gstride) {
+                ws.tmin[v] = kNoEdge;
+                ws.tpar[v] = (int32_t)v;
+            }
+        }
         // compress, with extra pointer-jumping passes while chains are deep
         for (uint32_t pass = 0;; pass++) {
             if (bid == 0 && threadIdx.x == 0)
@@ -874,19 +937,7 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
                 c->stat_m[r + 1] = m_t;
                 c->stat_n[r + 1] = n_next;
             }
-            // team size: one CTA per kTailEdgesPerThread edges a thread
-            constexpr uint32_t kPerCta = kTailEdgesPerThread * kFT;
-            uint32_t team = (m_t + kPerCta - 1) / kPerCta;
-            team = team < 1 ? 1 : (team > nb ? nb : team);
-            if (bid < team) {
-                if (team == 1) {  // per-component arrays in CTA 0's shared stage
-                    unsigned long long *smin = (unsigned long long *)sm.stage;
-                    int32_t *spar = (int32_t *)(smin + kTailMaxN);
-                    tail_solve(ws, c, n_next, m_t, r + 1, 1, smin, spar);
-                } else {
-                    tail_solve(ws, c, n_next, m_t, r + 1, team, ws.tmin, ws.tpar);
-                }
-            }
+            tail_rounds<kFT>(ws, c, n_next, m_t, r + 1, sm);
             mark_work(c);
             grid_sync(ws.bar, gen, status);
             log_phase(c, PH_TAIL, r + 1);
@@ -1131,7 +1182,8 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 8);
     b += align_up((size_t)kTailMaxN * kTailMaxN * 8);   // pair table
     b += 2 * align_up((size_t)kTailMaxPairs * 16);      // tail lists
-    b += align_up((size_t)kTailMaxN * 8) + align_up((size_t)kTailMaxN * 4);
+    b += align_up((size_t)kTailMaxN * 8) + 2 * align_up((size_t)kTailMaxN * 4);
+    b += align_up((size_t)kTailMaxPairs * 4);  // touched slots
     return b;
 }
 
@@ -1287,6 +1339,8 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.tl[1] = (uint4 *)take((size_t)kTailMaxPairs * 16);
     s.ws.tmin = (unsigned long long *)take((size_t)kTailMaxN * 8);
     s.ws.tpar = (int32_t *)take((size_t)kTailMaxN * 4);
+    s.ws.tnid = (int32_t *)take((size_t)kTailMaxN * 4);
+    s.ws.ttouch = (uint32_t *)take((size_t)kTailMaxPairs * 4);
     s.ws.n_cap = n_cap;
     s.ws.m_cap = m_cap;
     MST_TRY(cudaMemset(s.ws.ctl, 0, sizeof(Ctl)));

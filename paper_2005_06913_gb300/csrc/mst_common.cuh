@@ -103,7 +103,8 @@ struct Ws {
     int32_t *lab;      // new id of each component after compression
     uint32_t *mst_bits;
     uint32_t *epos;            // position of each live edge in the current list, by input id
-    unsigned long long *desc;  // look-back descriptors (emit)
+    unsigned long long *desc;  // look-back descriptors (emit of the graph schedule)
+    uint32_t *emit_cnt;        // tree edges per emit chunk (fused schedule)
     uint32_t *bar;             // grid-barrier counters of the fused kernel
     unsigned long long *pair_tab;  // lightest key per component pair (tail)
     uint4 *tl[2];                  // tail edge lists (a, b, weight_bits, input id)

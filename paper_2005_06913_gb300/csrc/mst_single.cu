@@ -464,6 +464,110 @@ __device__ __forceinline__ void emit_tile(const Ws &ws, Ctl *c, uint32_t tile, u
     __syncthreads();
 }
 
+// Emit of the fused schedule, in two passes with a grid barrier between
+// them instead of a look-back: first every chunk of kEmitWords bit words
+// counts its tree edges (one warp a chunk); then each CTA takes a contiguous
+// range of chunks, sums the counts of all chunks before it, and writes the
+// ids of its chunks in order.
+__device__ __forceinline__ void emit_count(const Ws &ws, uint32_t words, uint32_t nch,
+                                           uint32_t gw, uint32_t nw)
+{
+    const int lane = threadIdx.x & 31;
+    for (uint32_t t = gw; t < nch; t += nw) {
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kEmitWords / 32; k++) {
+            const uint32_t i = t * kEmitWords + k * 32 + lane;
+            cnt += i < words ? __popc(__ldcg(ws.mst_bits + i)) : 0u;
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0)
+            ws.emit_cnt[t] = cnt;
+    }
+}
+
+// Writes the ids of chunk t at out[ex...] (ascending); returns its count.
+__device__ __forceinline__ uint32_t emit_chunk(const Ws &ws, Ctl *c, uint32_t t, uint32_t ex,
+                                               uint32_t words, uint32_t cap, int32_t *out,
+                                               TileSmem &sm)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
+    const uint32_t i = t * kEmitWords + threadIdx.x;
+    const uint32_t wv = (threadIdx.x < kEmitWords && i < words) ? __ldcg(ws.mst_bits + i) : 0u;
+    const uint32_t cnt = __popc(wv);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        sm.s32[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < nwarps ? sm.s32[lane] : 0u;
+        uint32_t inc2 = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc2, o);
+            if (lane >= o)
+                inc2 += y;
+        }
+        if (lane < nwarps)
+            sm.s32[lane] = inc2 - v;
+        if (lane == 31)
+            sm.s32[32] = inc2;
+    }
+    __syncthreads();
+    const uint32_t total = sm.s32[32];
+    uint32_t pos = sm.s32[warp] + incl - cnt;
+    uint32_t *ids = (uint32_t *)sm.stage;
+    uint32_t bits = wv;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        ids[pos++] = i * 32u + (uint32_t)b;
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
+        if (ex + k < cap)
+            out[ex + k] = (int32_t)ids[k];
+        else
+            atomicOr(&c->status, ST_INTERNAL);  // more tree edges than n-1
+    }
+    __syncthreads();
+    return total;
+}
+
+template <int kFT>
+__device__ __forceinline__ void emit_range(const Ws &ws, Ctl *c, uint32_t nch, uint32_t words,
+                                           uint32_t cap, int32_t *out, TileSmem &sm)
+{
+    const uint32_t per = (nch + gridDim.x - 1) / gridDim.x;
+    const uint32_t t0 = blockIdx.x * per;
+    const uint32_t t1 = t0 + per < nch ? t0 + per : nch;
+    if (t0 >= t1)
+        return;
+    uint32_t part = 0;
+    for (uint32_t t = threadIdx.x; t < t0; t += kFT)
+        part += __ldcg(ws.emit_cnt + t);
+    part = __reduce_add_sync(0xffffffffu, part);
+    if ((threadIdx.x & 31) == 0)
+        sm.s32[threadIdx.x >> 5] = part;
+    __syncthreads();
+    uint32_t ex = 0;
+#pragma unroll
+    for (int k = 0; k < kFT / 32; k++)
+        ex += sm.s32[k];
+    __syncthreads();
+    for (uint32_t t = t0; t < t1; t++)
+        ex += emit_chunk(ws, c, t, ex, words, cap, out, sm);
+    if (t1 == nch && threadIdx.x == 0)
+        c->emitted = ex;
+}
+
 // Final checks of a solve: |M| = n - #components, disconnected flag.
 __device__ __forceinline__ void finish(Ctl *c, int64_t *out_count, uint32_t emitted,
                                        uint32_t n, uint32_t comps)
@@ -836,10 +940,8 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
 
 // The whole solve in one cooperative launch of kFT-thread CTAs (64
 // registers a thread at any size: 256 x 4, 512 x 2 or 1024 x 1 per SM).
-// Tiles are assigned statically (warp tile t to global warp t mod warps, emit
-// tile t to CTA t mod grid, in increasing order), so every look-back wait of
-// emit is on a tile whose CTA is resident and makes progress.  Larger CTAs
-// make fewer arrivals at each grid barrier.
+// Warp tiles are assigned statically (tile t to global warp t mod warps);
+// no phase waits on another CTA except at the grid barriers.
 template <int kFT>
 __global__ void __launch_bounds__(kFT, 1024 / kFT)
 k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_t *out,
@@ -853,7 +955,6 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
     const size_t gtid = (size_t)bid * kFT + threadIdx.x, gstride = (size_t)nb * kFT;
     const uint32_t gw = bid * kFW + (threadIdx.x >> 5), nw = nb * kFW;  // global warp
     uint32_t gen = 0;  // barrier count (the barrier itself keeps no generation)
-    uint32_t ep = c->epoch;
     log_phase(c, PH_START);
     init_range(ws, n, m, gtid, gstride);
     mark_work(c);
@@ -975,13 +1076,13 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             break;
         }
     }
-    // emit
+    // emit: count per chunk, barrier, write
     const uint32_t words = (m + 31u) >> 5;
     const uint32_t nte = (words + kEmitWords - 1) / kEmitWords;
     const uint32_t cap = n > 0 ? n - 1 : 0;
-    for (uint32_t t = bid; t < nte; t += nb)
-        emit_tile(ws, c, t, nte, ep, words, cap, out, sm);
-    ep++;
+    emit_count(ws, words, nte, gw, nw);
+    grid_sync(ws.bar, gen, status);
+    emit_range<kFT>(ws, c, nte, words, cap, out, sm);
     mark_work(c);
     grid_sync(ws.bar, gen, status);
     log_phase(c, PH_EMIT, r);
@@ -990,7 +1091,6 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         c->round = r + 1;
         c->n_cur = n_cur;
         c->m_cur = 0;
-        c->epoch = ep;
     }
 }
 
@@ -1180,6 +1280,7 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += align_up((((size_t)m_cap + 31) / 32) * 4);
     b += align_up((size_t)m_cap * 4);  // edge positions by id
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 8);
+    b += align_up((size_t)desc_capacity(n_cap, m_cap) * 4);  // emit chunk counts
     b += align_up((size_t)kTailMaxN * kTailMaxN * 8);   // pair table
     b += 2 * align_up((size_t)kTailMaxPairs * 16);      // tail lists
     b += align_up((size_t)kTailMaxN * 8) + 2 * align_up((size_t)kTailMaxN * 4);
@@ -1334,6 +1435,7 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.epos = (uint32_t *)take((size_t)m_cap * 4);
     s.ws.desc_cap = desc_capacity(n_cap, m_cap);
     s.ws.desc = (unsigned long long *)take((size_t)s.ws.desc_cap * 8);
+    s.ws.emit_cnt = (uint32_t *)take((size_t)s.ws.desc_cap * 4);
     s.ws.pair_tab = (unsigned long long *)take((size_t)kTailMaxN * kTailMaxN * 8);
     s.ws.tl[0] = (uint4 *)take((size_t)kTailMaxPairs * 16);
     s.ws.tl[1] = (uint4 *)take((size_t)kTailMaxPairs * 16);

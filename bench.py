@@ -47,22 +47,32 @@ def workload(cfg: int):
     return g, names[cfg]
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/ncu_traffic.txt: "kernel source_sha256 bytes_per_launch"),
-    or None when absent or taken on different kernel source."""
+def kernel_source_sha() -> str:
+    """sha256 prefix of the sources that define the fused single-graph kernel
+    (its tile bodies and device helpers)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    if not os.path.exists(p):
-        return None
     src = os.path.join(ROOT, "paper_2005_06913_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
+    for f in ("mst_common.cuh", "mst_single.cu"):
         h.update(open(os.path.join(src, f), "rb").read())
-    sha = h.hexdigest()[:16]
+    return h.hexdigest()[:16]
+
+
+TRAFFIC_WORKLOAD = {1: None, 2: "grid2d_1024x1024", 3: "rmat_scale22"}
+
+
+def traffic_for(kernel: str, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/ncu_traffic.txt: "kernel source_sha256 bytes workload"),
+    or None when absent or taken on different kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if workload is None or not os.path.exists(p):
+        return None
+    sha = kernel_source_sha()
     for line in open(p):
         f = line.split()
-        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == sha:
+        if (len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == sha
+                and f[3] == workload):
             return float(f[2])
     return None
 
@@ -322,7 +332,8 @@ def run_ours(args):
                                                     dom["total_ms"] * 1e-3, dom["launches"])
     achieved = dom_bytes / dom_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic_for(dom_name),
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": traffic_for(dom_name, TRAFFIC_WORKLOAD.get(args.config)),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",
                 "launches_per_step": dom_launches,
                 "alg_bytes_per_launch": dom_bytes / max(dom_launches, 1),

@@ -168,35 +168,26 @@ __device__ __forceinline__ void red_or_u32(uint32_t *p, uint32_t v)
 // that cannot win: values at p only decrease, so a cached (possibly older)
 // value is never below the true one, and skipping key >= cached is exact.
 // On hot components this turns most same-address atomics into cache hits.
-__device__ __forceinline__ void offer_min(unsigned long long *p, unsigned long long key)
+__device__ __forceinline__ bool offer_min(unsigned long long *p, unsigned long long key)
 {
-    if (key < __ldca(p))
+    if (key < __ldca(p)) {
         red_min_u64(p, key);
+        return true;
+    }
+    return false;
 }
 
 // Whether offers go through the filtering load: measured on GB300, a plain
 // red.min.u64 sustains ~157 G/s on distinct addresses but ~1.5 G/s on one
 // hot address, while the filtered offer costs ~15-65% on distinct addresses
 // and is 25x faster on a hot one.  Filter when a target receives many
-// offers on average (hot spots likely): at least 8 per target.
+// offers on average (hot spots likely): at least 16 per target (swept over
+// 2..32 on the grid and R-MAT workloads: 16 is fastest on both; at 32 the
+// R-MAT round-0 find-min runs unfiltered into its hubs and takes twice as
+// long).
 __device__ __forceinline__ bool use_filter(uint32_t m_cur, uint32_t targets)
 {
-    return 2ull * m_cur >= 8ull * (unsigned long long)(targets > 0 ? targets : 1);
-}
-
-// Warp-cooperative offer: lanes in `active` (all calling) offer keys to
-// components c; lanes naming the same component first agree on their
-// minimum (64-bit key as high word, then low word), and one lane per
-// distinct component offers it.
-__device__ __forceinline__ void offer_min_grouped(unsigned long long *arr, uint32_t active,
-                                                  uint32_t c, unsigned long long key)
-{
-    const uint32_t grp = __match_any_sync(active, c);
-    const uint32_t hi = __reduce_min_sync(grp, (uint32_t)(key >> 32));
-    const uint32_t lo = __reduce_min_sync(grp, (uint32_t)(key >> 32) == hi ? (uint32_t)key
-                                                                           : 0xffffffffu);
-    if ((threadIdx.x & 31) == (uint32_t)(__ffs(grp) - 1))
-        offer_min(arr + c, ((unsigned long long)hi << 32) | lo);
+    return 2ull * m_cur >= 16ull * (unsigned long long)(targets > 0 ? targets : 1);
 }
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p)

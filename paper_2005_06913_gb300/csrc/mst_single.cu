@@ -132,12 +132,6 @@ __device__ __forceinline__ void find0_range(const Ws &ws, const int32_t *src, co
 // involved, so a warp waiting on memory or on its predecessor never holds
 // up the other warps of its CTA.
 constexpr int kHookIpl = 4, kCompIpl = 8;
-// Below this many components, compaction would combine a warp's offers per
-// component (match + reduce) before touching memory.  Measured on GB300 it
-// costs more than it saves on both the grid and the R-MAT workloads (the
-// filtered offer already removes the hot-spot atomics), so it is off.
-constexpr uint32_t kGroupedMaxComponents = 0u;  // measured: grouping costs more than it saves
-
 constexpr int kHookWTile = 32 * kHookIpl, kCompWTile = 32 * kCompIpl;
 
 // Hook one warp tile of components (Section 2.1, the union step) and give
@@ -372,8 +366,6 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
         ex = atomicAdd(&c->cnt_m[round], total);
     ex = __shfl_sync(0xffffffffu, ex, 0);
     const uint32_t lt = lanemask_lt();
-    // few components left: many lanes of a warp offer to the same one
-    const bool grouped = n_next <= kGroupedMaxComponents;
     const bool filtered = use_filter(m_cur, n_next);
     uint32_t run = ex;
 #pragma unroll
@@ -381,18 +373,19 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
         if ((mask[j] >> lane) & 1u) {
             const uint32_t pos = run + __popc(mask[j] & lt);
             enext[pos] = rec[j];
-            __stcg(ws.epos + rec[j].w, pos);
             const unsigned long long key = make_key(rec[j].z, rec[j].w);
-            if (grouped) {
-                offer_min_grouped(mnext, mask[j], rec[j].x, key);
-                offer_min_grouped(mnext, mask[j], rec[j].y, key);
-            } else if (filtered) {
-                offer_min(&mnext[rec[j].x], key);
-                offer_min(&mnext[rec[j].y], key);
+            // Only an edge that passes a filter can end up as a minimum (the
+            // minimum only decreases), so only those record their position.
+            bool may_win = true;
+            if (filtered) {
+                may_win = offer_min(&mnext[rec[j].x], key);
+                may_win |= offer_min(&mnext[rec[j].y], key);
             } else {
                 red_min_u64(&mnext[rec[j].x], key);
                 red_min_u64(&mnext[rec[j].y], key);
             }
+            if (may_win)
+                __stcg(ws.epos + rec[j].w, pos);
         }
         run += __popc(mask[j]);
     }

@@ -539,12 +539,14 @@ def run_serving(args):
     rng = np.random.default_rng(5)
     budget = 120 << 30
     results = []
+    streams_of_rate = {}
     for rate in [float(x) for x in args.rates.split(",")]:
         h = B.mst_create(0, budget)
         B.mst_server_start(h, args.streams, args.max_batch)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * args.seconds) + 1))
         arrivals = arrivals[arrivals < args.seconds]
         picks = rng.integers(0, pool.G, arrivals.shape[0])
+        streams_of_rate[rate] = (arrivals, picks)
         tickets, lat, done_t = {}, [], []
         slot_busy = {}
         errors = 0
@@ -579,6 +581,40 @@ def run_serving(args):
         p50, p99 = _percentiles(lat)
         results.append({"rate_offered": rate, "requests": len(lat), "errors": errors,
                         "graphs_per_s": len(lat) / elapsed, "latency_ms": {"p50": p50, "p99": p99}})
+    # the same arrival streams served one solve at a time (single-graph
+    # kernel, one stream, FIFO): what the same kernels give without batching.
+    # A stream the server cannot keep up with is cut off after 3x its span;
+    # requests still queued then count with their waiting time so far (a
+    # lower bound, which favours this arm).
+    h = B.mst_create(0, 0)
+    sequential = []
+    for rate, (arrivals, picks) in streams_of_rate.items():
+        lat = []
+        t_start = time.perf_counter()
+        cut = 3.0 * args.seconds
+        served = 0
+        for k in range(arrivals.shape[0]):
+            now = time.perf_counter() - t_start
+            if now > cut:
+                lat.extend((now - arrivals[k:]) * 1e3)
+                break
+            while now < arrivals[k]:
+                if arrivals[k] - now > 5e-4:
+                    time.sleep(2e-4)
+                now = time.perf_counter() - t_start
+            g = int(picks[k])
+            e0, e1 = int(pool.edge_off[g]), int(pool.edge_off[g + 1])
+            n_g = int(pool.vtx_off[g + 1] - pool.vtx_off[g])
+            B.mst_solve_ex(h, B.MST_W_F32, n_g, e1 - e0, s[e0:], d[e0:], w[e0:], outs[0], cnts[0:])
+            torch.cuda.current_stream().synchronize()
+            lat.append((time.perf_counter() - t_start - arrivals[k]) * 1e3)
+            served += 1
+        span = time.perf_counter() - t_start
+        p50, p99 = _percentiles(lat)
+        sequential.append({"rate_offered": rate, "requests": int(arrivals.shape[0]),
+                           "served": served, "graphs_per_s": served / span,
+                           "latency_ms": {"p50": p50, "p99": p99}})
+    B.mst_destroy(h)
     # one solve at a time on one stream, same pool, back to back (its best case)
     h = B.mst_create(0, 0)
     one = []
@@ -605,6 +641,7 @@ def run_serving(args):
                        "streams": args.streams, "max_batch": args.max_batch,
                        "memory_budget_bytes": budget},
             "sweep": results,
+            "same_streams_one_solve_at_a_time": sequential,
             "one_solve_at_a_time": {"graphs_per_s": len(one) / (sum(one) * 1e-3),
                                     "latency_ms": {"p50": q50, "p99": q99},
                                     "sample": f"first {len(one)} pool graphs, back to back"}}

@@ -253,9 +253,10 @@ mst_status mst_solve_noalloc(mst_weight_type wt, int32_t n, int64_t m,
  * admits new requests as soon as a stream and memory are free, so solves of
  * requests that arrive while others run overlap on the GPU.  max_batch caps
  * the graphs per launch.  A request with more than 131072 edges is not
- * batched: it is solved alone by the fused single-graph kernel (half the
- * persistent grid) in a workspace owned by its stream, one such request at a
- * time, while small requests keep being batched past it on other streams.
+ * batched: it is solved alone by the fused single-graph kernel in a workspace
+ * owned by its stream (on the whole co-resident grid when nothing else is in
+ * flight, else on half of it), one such request at a time, while small
+ * requests keep being batched past it on other streams.
  */
 mst_status mst_server_start(mst_handle h, int streams, int max_batch);
 

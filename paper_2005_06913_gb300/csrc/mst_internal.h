@@ -52,7 +52,7 @@ void single_release(Single &s);
 // Queues one solve on `stream` (arguments already validated).
 cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n,
-                          uint32_t m, cudaStream_t stream);
+                          uint32_t m, cudaStream_t stream, int grid = 0);
 double single_alg_bytes(const Ctl &c);
 // Per-phase times of the last fused solve (its own phase log; synchronous).
 cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<KernelProfile> &prof);

@@ -11,9 +11,12 @@
 // requests that arrive while other batches run on the GPU are admitted as
 // soon as a slot and memory free up, and their solves overlap on the device.
 // Large requests (more than kServeBigM edges) are not batched: one CTA per
-// graph would take tens of milliseconds on them.  A slot solves such a
-// request alone with the fused multi-CTA single-graph kernel in its own
-// workspace, while other slots keep serving batches.
+// graph would take tens of milliseconds on them.  Medium ones (more than
+// kServeMidM edges) wait for the fused lane too unless its queue is long.
+// The lane solves one such request at a time, on a slot's stream, with the
+// fused multi-CTA single-graph kernel in the server's one lane workspace:
+// on the whole co-resident grid when nothing else is in flight, else on
+// half of it, while other slots keep serving batches.
 // Each request's result is the same as a solve of that graph alone: the
 // minimum spanning tree under the (weight, edge id) order is unique.
 #include <cuda_runtime.h>
@@ -27,11 +30,11 @@
 
 namespace mst {
 
-constexpr int64_t kServeBigM = 131072;  // larger requests get the fused kernel
-constexpr int kServeFusedThreads = 512;  // one such CTA per SM leaves room for batches
+constexpr int64_t kServeBigM = 131072;  // larger requests always get the fused kernel
+constexpr int64_t kServeMidM = 16384;   // larger ones wait for it ...
+constexpr int kServeLaneDepth = 4;       // ... unless this many are ahead of them
 
 struct Slot {
-    Single single;                // fused-kernel workspace for large requests
     bool big = false;             // the request in flight is a large one
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -59,6 +62,7 @@ struct Server {
     std::unordered_map<uint64_t, Outcome> results;
     std::unordered_map<uint64_t, double> submit_us;
     std::vector<Slot> slots;
+    Single lane;  // fused-kernel workspace of the (single) large-request lane
     int max_batch = 256;
     uint64_t next_ticket = 1;
     size_t in_use = 0;
@@ -79,7 +83,7 @@ static void complete_slot(Server &S, Slot &sl)
     const double t = now_us();
     uint32_t bits = 0;
     if (sl.big) {
-        cudaMemcpy(&bits, &sl.single.ws.ctl->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&bits, &S.lane.ws.ctl->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
     } else {
         cudaMemcpy(&bits, sl.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost);
         cudaFreeAsync(sl.ws, sl.stream);
@@ -107,7 +111,10 @@ static void complete_slot(Server &S, Slot &sl)
 }
 
 // Takes queued requests for one launch (lock held).  Large requests form
-// their own FIFO lane with at most one in flight: the fused kernel's grid
+// their own FIFO lane with at most one in flight; that lane also takes the
+// oldest medium request, which one CTA of a batch would solve several times
+// slower.  A medium request goes to a batch only when kServeLaneDepth
+// requests for the lane are queued ahead of it.  The fused kernel's grid
 // barrier needs all of its CTAs resident at once, and two fused grids that
 // are each partly resident would wait on each other until the barrier gives
 // up.  One fused grid next to batched kernels (which never wait on anything)
@@ -128,20 +135,23 @@ static std::vector<Request> take_batch(Server &S, Slot &sl, size_t budget, bool 
     *big = false;
     if (!S.big_inflight) {
         for (auto it = S.pending.begin(); it != S.pending.end();) {
-            if (it->m <= kServeBigM) {
+            if (it->m <= kServeMidM) {
                 ++it;
                 continue;
             }
-            const size_t have = sl.single.base ? sl.single.bytes : 0;
+            const bool large = it->m > kServeBigM;  // else a batch may take it
+            const size_t have = S.lane.base ? S.lane.bytes : 0;
             const size_t need = single_bytes((uint32_t)std::max<int64_t>(it->n, 1024),
                                              (uint32_t)std::max<int64_t>(it->m, 1024));
-            if (budget && need > budget) {  // can never be admitted
+            if (budget && need > budget && large) {  // can never be admitted
                 reject(S, it);
                 it = S.pending.erase(it);
                 continue;
             }
-            if (budget && need > have && S.in_use - have + need > budget)
-                break;  // wait for memory; small requests may still go
+            if (budget && need > have && S.in_use - have + need > budget) {
+                ++it;  // wait for memory (a medium one goes to a batch instead)
+                continue;
+            }
             batch.push_back(*it);
             S.pending.erase(it);
             *big = true;
@@ -149,8 +159,10 @@ static std::vector<Request> take_batch(Server &S, Slot &sl, size_t budget, bool 
         }
     }
     size_t bytes = 4096 + 64 * 4;  // control block and order list slack
+    int lane_ahead = 0;            // requests queued for the lane so far
     for (auto it = S.pending.begin(); it != S.pending.end() && (int)batch.size() < S.max_batch;) {
-        if (it->m > kServeBigM) {
+        if (it->m > kServeBigM || (it->m > kServeMidM && lane_ahead < kServeLaneDepth)) {
+            lane_ahead += it->m > kServeMidM ? 1 : 0;
             ++it;
             continue;
         }
@@ -170,23 +182,27 @@ static std::vector<Request> take_batch(Server &S, Slot &sl, size_t budget, bool 
 }
 
 // A large request on the slot's fused-kernel workspace (grown if needed).
-static cudaError_t launch_big(Server &S, Slot &sl, const Request &r)
+static cudaError_t launch_big(Server &S, Slot &sl, const Request &r, bool alone)
 {
     const uint32_t n = (uint32_t)r.n, m = (uint32_t)r.m;
-    if (!sl.single.base || n > sl.single.ws.n_cap || m > sl.single.ws.m_cap) {
-        const size_t before = sl.single.base ? sl.single.bytes : 0;
-        sl.single.fused_blocks_per_sm = 1;
-        sl.single.fused_threads = kServeFusedThreads;
-        cudaError_t e = single_reserve(sl.single, S.h->device, n, m);
+    Single &lane = S.lane;
+    if (!lane.base || n > lane.ws.n_cap || m > lane.ws.m_cap) {
+        const size_t before = lane.base ? lane.bytes : 0;
+        lane.fused_blocks_per_sm = 4;
+        lane.fused_threads = 256;
+        cudaError_t e = single_reserve(lane, S.h->device, n, m);
         std::lock_guard<std::mutex> lk(S.mu);
-        S.in_use = S.in_use - before + (sl.single.base ? sl.single.bytes : 0);
+        S.in_use = S.in_use - before + (lane.base ? lane.bytes : 0);
         if (e != cudaSuccess)
             return e;
     }
     if (n == 0)
         return cudaMemsetAsync(r.out_count, 0, sizeof(int64_t), sl.stream);
-    cudaError_t e = single_launch(sl.single, r.src, r.dst, r.w, r.wt, r.out, r.out_count, n, m,
-                                  sl.stream);
+    // the whole co-resident grid when nothing else runs, else half of it
+    // (two CTAs per SM), which leaves room for batches on the other slots
+    const int grid = alone ? lane.grid_fused : lane.grid_fused / 2;
+    cudaError_t e = single_launch(lane, r.src, r.dst, r.w, r.wt, r.out, r.out_count, n, m,
+                                  sl.stream, grid);
     if (e == cudaSuccess)
         e = cudaEventRecord(sl.done, sl.stream);
     sl.tickets.assign(1, r.ticket);
@@ -278,12 +294,14 @@ static void server_loop(Server *Sp)
                 bytes += request_bytes((uint32_t)r.n, (uint32_t)r.m);
         if (!big)
             S.in_use += bytes + 4096;
+        const bool alone = S.inflight == 0;
         S.inflight++;
         S.big_inflight |= big;
         free_slot->busy = true;
         free_slot->big = big;
         lk.unlock();
-        cudaError_t e = big ? launch_big(S, *free_slot, batch[0]) : launch_batch(S, *free_slot, batch);
+        cudaError_t e =
+            big ? launch_big(S, *free_slot, batch[0], alone) : launch_batch(S, *free_slot, batch);
         if (e != cudaSuccess) {
             cudaGetLastError();
             std::lock_guard<std::mutex> g(S.mu);
@@ -403,8 +421,8 @@ mst_status server_stop(mst_handle h)
             cudaFreeHost(sl.h_desc);
         if (sl.d_desc)
             cudaFree(sl.d_desc);
-        single_release(sl.single);
     }
+    single_release(S->lane);
     const mst_status st = S->error == cudaSuccess ? MST_OK : MST_ERR_CUDA;
     delete S;
     h->server = nullptr;

@@ -1455,7 +1455,7 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     if (s.grid_fused > kMaxGridBlocks)
         s.grid_fused = kMaxGridBlocks;
     s.solves = 0;
-    return build_graph(s);
+    return cudaSuccess;  // the graph schedule's CUDA graph is built on first use
 }
 
 // Host part of a solve shared by both schedules: keeps the descriptor
@@ -1476,17 +1476,21 @@ static cudaError_t begin_solve(Single &s, cudaStream_t stream)
 
 cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n, uint32_t m,
-                          cudaStream_t stream)
+                          cudaStream_t stream, int grid)
 {
+    // the fused kernel runs on any grid up to the co-resident one
+    const int g = grid > 0 && grid < s.grid_fused ? grid : s.grid_fused;
     MST_TRY(begin_solve(s, stream));
     const uint32_t vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)w) & 15u) == 0 ? 1u : 0u;
     if (s.schedule != 2) {
         const uint32_t *wp = (const uint32_t *)w;
         void *args[] = {(void *)&s.ws, (void *)&src, (void *)&dst, (void *)&wp, (void *)&out,
                         (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec};
-        return cudaLaunchCooperativeKernel(fused_kernel(s.fused_threads), dim3(s.grid_fused),
+        return cudaLaunchCooperativeKernel(fused_kernel(s.fused_threads), dim3(g),
                                            dim3(s.fused_threads), args, 0, stream);
     }
+    if (!s.exec)
+        MST_TRY(build_graph(s));
     k_init<<<s.grid_stream, kThreads, 0, stream>>>(s.ws, src, dst, w, out, out_count, n, m, wt,
                                                    vec);
     MST_TRY(cudaGetLastError());

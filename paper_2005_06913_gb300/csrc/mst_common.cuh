@@ -29,8 +29,11 @@ constexpr int kChaseLimit = 64;               // pointer hops per thread per pas
 constexpr uint32_t kMaxJumpPasses = 64;       // > log2(2^31): pointer jumping ends sooner
 constexpr uint32_t kSpinLimit = 1u << 22;     // iterations of any device wait
 constexpr int kMaxPhaseLog = 256;             // phase-log entries kept per fused solve
-constexpr uint32_t kTailMaxN = 1024;          // components at which the tail takes over
+constexpr uint32_t kTailMaxN = 1024;          // components at which the tail takes over (2048
+                                              // measured slower: multi-CTA tail rounds cost
+                                              // more than the grid round they save)
 constexpr uint32_t kTailMaxPairs = kTailMaxN * (kTailMaxN - 1) / 2;
+constexpr uint32_t kTailLocalN = 1024;        // a one-CTA tail keeps arrays in shared memory
 
 // Phase kinds of the fused solve's phase log.
 enum : uint8_t { PH_START = 0, PH_INIT, PH_FIND0, PH_HOOK, PH_COMPRESS, PH_COMPACT, PH_EMIT,

@@ -46,10 +46,12 @@ namespace mst {
 constexpr int kEmitWords = 128;  // bit words per emit tile: <= 4096 ids, fits the stage
 
 struct TileSmem {
-    uint4 stage[kTile];  // survivors of a compaction tile / ids of an emit tile
+    uint4 stage[kTile];  // ids of an emit tile / per-component arrays of a one-CTA tail
     uint32_t s32[33];
     uint32_t s_tile, s_excl, s_flag;
 };
+static_assert(kTailLocalN * (8 + 4 + 4) <= sizeof(uint4) * kTile,
+              "a one-CTA tail's minima, pointers and new ids fit the stage");
 
 // ------------------------------------------------------------ tile bodies
 
@@ -664,7 +666,8 @@ __device__ __forceinline__ void log_phase(Ctl *c, uint8_t kind, uint32_t round =
 // So parallel edges are merged every round and a round costs O(list), not
 // O(table).  The rounds run on a team of CTAs sized to the list (one CTA per
 // kTailEdgesPerThread edges a thread, never growing): a team of one keeps
-// the per-component arrays in shared memory and syncs with block barriers,
+// the per-component arrays in shared memory once at most kTailLocalN
+// components are left, and syncs with block barriers,
 // a larger team keeps them in global memory and syncs with a barrier among
 // its own CTAs.
 
@@ -804,10 +807,10 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
         team = team < 1 ? 1 : (team > team_prev ? team_prev : team);
         if (bid >= team)
             return;
-        if (team == 1 && !local) {  // CTA 0 goes on alone: arrays into shared memory
+        if (team == 1 && !local && n_r <= kTailLocalN) {  // CTA 0 alone: arrays into smem
             unsigned long long *smin = (unsigned long long *)sm.stage;
-            int32_t *spar = (int32_t *)(smin + kTailMaxN);
-            int32_t *snid = spar + kTailMaxN;
+            int32_t *spar = (int32_t *)(smin + kTailLocalN);
+            int32_t *snid = spar + kTailLocalN;
             for (uint32_t v = threadIdx.x; v < n_r; v += kFT) {
                 smin[v] = __ldcg(ws.tmin + v);
                 spar[v] = (int32_t)v;
@@ -1263,6 +1266,20 @@ static uint32_t desc_capacity(uint32_t n_cap, uint32_t m_cap)
 
 static const int kMaxGridBlocks = 152 * 8 * 2;  // bound for the barrier counters
 
+// Tail capacities: the pair table covers up to min(kTailMaxN, n) components,
+// and no pair list is longer than the edge list (a pair needs an edge).
+static size_t tail_n_cap(uint32_t n_cap)
+{
+    return n_cap < kTailMaxN ? n_cap : kTailMaxN;
+}
+
+static size_t tail_pairs_cap(uint32_t n_cap, uint32_t m_cap)
+{
+    const size_t tn = tail_n_cap(n_cap);
+    const size_t pairs = tn * (tn - 1) / 2;
+    return pairs < m_cap ? pairs : m_cap;
+}
+
 size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
 {
     size_t b = align_up(sizeof(Ctl));
@@ -1274,10 +1291,11 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += align_up((size_t)m_cap * 4);  // edge positions by id
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 8);
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 4);  // emit chunk counts
-    b += align_up((size_t)kTailMaxN * kTailMaxN * 8);   // pair table
-    b += 2 * align_up((size_t)kTailMaxPairs * 16);      // tail lists
+    const size_t tn = tail_n_cap(n_cap), tp = tail_pairs_cap(n_cap, m_cap);
+    b += align_up(tn * tn * 8);                  // pair table
+    b += 2 * align_up(tp * 16);                  // tail lists
     b += align_up((size_t)kTailMaxN * 8) + 2 * align_up((size_t)kTailMaxN * 4);
-    b += align_up((size_t)kTailMaxPairs * 4);  // touched slots
+    b += align_up(tp * 4);                       // touched slots
     return b;
 }
 
@@ -1429,13 +1447,14 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.desc_cap = desc_capacity(n_cap, m_cap);
     s.ws.desc = (unsigned long long *)take((size_t)s.ws.desc_cap * 8);
     s.ws.emit_cnt = (uint32_t *)take((size_t)s.ws.desc_cap * 4);
-    s.ws.pair_tab = (unsigned long long *)take((size_t)kTailMaxN * kTailMaxN * 8);
-    s.ws.tl[0] = (uint4 *)take((size_t)kTailMaxPairs * 16);
-    s.ws.tl[1] = (uint4 *)take((size_t)kTailMaxPairs * 16);
+    const size_t tn = tail_n_cap(n_cap), tp = tail_pairs_cap(n_cap, m_cap);
+    s.ws.pair_tab = (unsigned long long *)take(tn * tn * 8);
+    s.ws.tl[0] = (uint4 *)take(tp * 16);
+    s.ws.tl[1] = (uint4 *)take(tp * 16);
     s.ws.tmin = (unsigned long long *)take((size_t)kTailMaxN * 8);
     s.ws.tpar = (int32_t *)take((size_t)kTailMaxN * 4);
     s.ws.tnid = (int32_t *)take((size_t)kTailMaxN * 4);
-    s.ws.ttouch = (uint32_t *)take((size_t)kTailMaxPairs * 4);
+    s.ws.ttouch = (uint32_t *)take(tp * 4);
     s.ws.n_cap = n_cap;
     s.ws.m_cap = m_cap;
     MST_TRY(cudaMemset(s.ws.ctl, 0, sizeof(Ctl)));

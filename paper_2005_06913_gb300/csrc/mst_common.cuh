@@ -6,7 +6,7 @@
 // broken by edge id): key = (weight_bits << 32) | tag.  weight_bits is the
 // uint32 weight, or for float32 an order-preserving remap of the IEEE bits.
 // The single-graph solver tags with the input edge id itself and finds the
-// edge's record through a position-by-id map.  The batched solver tags with
+// edge's endpoints in an endpoints-by-id array.  The batched solver tags with
 // the edge's index in its live list; its compaction is stable, so position
 // order equals edge-id order among the edges still alive.  Either way the
 // minimum over keys is the minimum over (weight, edge id).
@@ -105,7 +105,7 @@ struct Ws {
     int32_t *nid;      // new dense id of each root
     int32_t *lab;      // new id of each component after compression
     uint32_t *mst_bits;
-    uint32_t *epos;            // position of each live edge in the current list, by input id
+    uint2 *eends;              // current endpoints of a possible minimum edge, by input id
     unsigned long long *desc;  // look-back descriptors (emit of the graph schedule)
     uint32_t *emit_cnt;        // tree edges per emit chunk (fused schedule)
     uint32_t *bar;             // grid-barrier counters of the fused kernel

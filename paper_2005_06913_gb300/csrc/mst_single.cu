@@ -21,9 +21,9 @@
 //     takes the root's new id.
 //   compact (Section 2.1 "Optimization", covered edges): edges whose two
 //     renamed endpoints coincide are dropped; each warp tile writes its
-//     survivors to a block of positions taken with one atomicAdd, records
-//     each survivor's position under its input id, and offers its keys for
-//     round r+1.
+//     survivors to a block of positions taken with one atomicAdd, and each
+//     survivor offers its key for round r+1 (one that may win records its
+//     new endpoints under its input id, for the next hook).
 // The rounds stop when no live edge is left; the tree edges are then emitted
 // in ascending id order.
 //
@@ -139,7 +139,7 @@ constexpr int kHookWTile = 32 * kHookIpl, kCompWTile = 32 * kCompIpl;
 // Hook one warp tile of components (Section 2.1, the union step) and give
 // the tile's roots new ids from the round's counter.  The minimum key's tag
 // is the input edge id: round 0 reads the input endpoints, later rounds the
-// edge's record at its recorded position.
+// endpoints the edge recorded under its id when it was offered.
 template <bool R0>
 __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, uint32_t round,
                                            uint32_t n_cur, const int32_t *src,
@@ -148,7 +148,6 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
     const int lane = threadIdx.x & 31;
     const unsigned long long *mcur = (round & 1) ? ws.mins[1] : ws.mins[0];
     unsigned long long *mnext = (round & 1) ? ws.mins[0] : ws.mins[1];
-    const uint4 *ecur = (round & 1) ? ws.E[1] : ws.E[0];
     int32_t *parent = ws.parent;
     const uint32_t base = tile * kHookWTile;
     unsigned long long k[kHookIpl];
@@ -171,7 +170,7 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
                 b[j] = (uint32_t)__ldg(dst + p);
                 id[j] = p;
             } else {
-                const uint4 r = ecur[__ldcg(ws.epos + p)];
+                const uint2 r = __ldcg(ws.eends + p);
                 a[j] = r.x;
                 b[j] = r.y;
                 id[j] = p;
@@ -311,8 +310,8 @@ __device__ __forceinline__ bool compress_range(const Ws &ws, uint32_t n_cur, boo
 // Compaction of one warp tile of round r's live edges fused with find-min
 // of round r+1: survivors are written from registers to a block of
 // positions taken from the round's counter (one contiguous run per row of
-// the tile), their positions are recorded by input id, and they offer their
-// (weight, id) keys with fire-and-forget reductions.
+// the tile), possible minima record their new endpoints by input id, and
+// they offer their (weight, id) keys with fire-and-forget reductions.
 template <bool R0>
 __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t tile,
                                               uint32_t round, uint32_t m_cur, uint32_t n_next,
@@ -377,7 +376,8 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
             enext[pos] = rec[j];
             const unsigned long long key = make_key(rec[j].z, rec[j].w);
             // Only an edge that passes a filter can end up as a minimum (the
-            // minimum only decreases), so only those record their position.
+            // minimum only decreases), so only those record their endpoints
+            // for the next hook.
             bool may_win = true;
             if (filtered) {
                 may_win = offer_min(&mnext[rec[j].x], key);
@@ -387,7 +387,7 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
                 red_min_u64(&mnext[rec[j].y], key);
             }
             if (may_win)
-                __stcg(ws.epos + rec[j].w, pos);
+                __stcg(ws.eends + rec[j].w, make_uint2(rec[j].x, rec[j].y));
         }
         run += __popc(mask[j]);
     }
@@ -1288,7 +1288,7 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += 2 * align_up((size_t)n_cap * 8);
     b += 3 * align_up((size_t)n_cap * 4);
     b += align_up((((size_t)m_cap + 31) / 32) * 4);
-    b += align_up((size_t)m_cap * 4);  // edge positions by id
+    b += align_up((size_t)m_cap * 8);  // endpoints of possible minima, by id
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 8);
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 4);  // emit chunk counts
     const size_t tn = tail_n_cap(n_cap), tp = tail_pairs_cap(n_cap, m_cap);
@@ -1443,7 +1443,7 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.nid = (int32_t *)take((size_t)n_cap * 4);
     s.ws.lab = (int32_t *)take((size_t)n_cap * 4);
     s.ws.mst_bits = (uint32_t *)take((((size_t)m_cap + 31) / 32) * 4);
-    s.ws.epos = (uint32_t *)take((size_t)m_cap * 4);
+    s.ws.eends = (uint2 *)take((size_t)m_cap * 8);
     s.ws.desc_cap = desc_capacity(n_cap, m_cap);
     s.ws.desc = (unsigned long long *)take((size_t)s.ws.desc_cap * 8);
     s.ws.emit_cnt = (uint32_t *)take((size_t)s.ws.desc_cap * 4);

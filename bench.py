@@ -269,7 +269,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     h = B.mst_create(dev, 0)
-    B.mst_set_single_schedule(h, 1 if args.schedule == "fused" else 2, 0, 0)
+    B.mst_set_single_schedule(h, 0 if args.schedule == "fused" else 2, 0, 0)
 
     def solve():
         st = B.mst_solve(h, g.n, g.m, src, dst, w, out, cnt, stream)

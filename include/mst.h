@@ -181,14 +181,16 @@ mst_status mst_profile_last_solve(mst_handle h, void *stream, mst_kernel_profile
                                   int32_t cap, int32_t *count);
 
 /*
- * Schedule of single-graph solves.  schedule: 0 = default (1), 1 = one
- * cooperative persistent launch per solve whose phases are separated by grid
- * barriers, 2 = one kernel per phase replayed from a CUDA graph whose round
- * loop is a device-side conditional WHILE node.  For schedule 1,
+ * Schedule of single-graph solves.  schedule: 0 = default: one cooperative
+ * persistent launch per solve whose phases are separated by grid barriers,
+ * with its shape chosen per solve (one CTA per SM: 256 threads up to 600,000
+ * edges, 1024 above); 1 = the same kernel with a fixed shape, where
  * block_threads (256, 512, 768 or 1024; 0 = keep, default 256) sets the CTA
  * size and blocks_per_sm (1..8, 0 = keep, default 4) the CTAs per SM, clamped
  * to what fits (64 registers a thread: 1024 threads a CTA fit once per SM,
- * 256 four times).  Results are identical under every setting.
+ * 256 four times); 2 = one kernel per phase replayed from a CUDA graph whose
+ * round loop is a device-side conditional WHILE node.  Results are identical
+ * under every setting.
  */
 mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm,
                                    int block_threads);

@@ -33,7 +33,8 @@ struct Single {
     int grid_fused = 0;     // co-resident grid of the fused cooperative kernel
     int fused_blocks_per_sm = 4;  // CTAs per SM of the fused kernel (clamped by occupancy)
     int fused_threads = 256;      // threads per CTA of the fused kernel
-    int schedule = 0;       // 0/1 fused cooperative kernel, 2 CUDA graph of kernels
+    int schedule = 0;       // 0 fused, shape per solve; 1 fused, fixed shape; 2 CUDA graph
+    int sms = 0;            // multiprocessors of the device
     uint64_t solves = 0;    // solves since the descriptors were last cleared
 };
 

@@ -188,6 +188,7 @@ static cudaError_t launch_big(Server &S, Slot &sl, const Request &r, bool alone)
     Single &lane = S.lane;
     if (!lane.base || n > lane.ws.n_cap || m > lane.ws.m_cap) {
         const size_t before = lane.base ? lane.bytes : 0;
+        lane.schedule = 1;  // fixed shape: the grid is chosen per launch below
         lane.fused_blocks_per_sm = 4;
         lane.fused_threads = 256;
         cudaError_t e = single_reserve(lane, S.h->device, n, m);

@@ -1402,6 +1402,14 @@ static int occupancy(const void *func, size_t smem, int threads = kThreads)
     return blocks;
 }
 
+// Edge count above which the automatic shape (schedule 0) takes 1024-thread
+// CTAs instead of 256-thread ones, one CTA per SM either way.  Measured on
+// GB300 (random graphs of 4K..4.5M edges, the grid and R-MAT workloads):
+// below ~0.6M edges one 256-thread CTA per SM is 12-20% faster than four
+// (fewer arrivals at each barrier, enough parallelism for the work); above,
+// one 1024-thread CTA per SM is fastest (R-MAT 22: 1.71 ms against 1.77 ms).
+constexpr uint32_t kAutoWideM = 600000;
+
 // The fused kernel for a CTA size (256, 512, 768 or 1024 threads).
 static const void *fused_kernel(int threads)
 {
@@ -1462,6 +1470,7 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     MST_TRY(cudaMemset(s.ws.desc, 0, (size_t)s.ws.desc_cap * 8));
     int sms = 0;
     MST_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    s.sms = sms;
     int occ_t = occupancy((const void *)k_compact<false>, 0);
     int occ_h = occupancy((const void *)k_hook<false>, 0);
     int occ = occ_t < occ_h ? occ_t : occ_h;
@@ -1498,15 +1507,20 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
                           cudaStream_t stream, int grid)
 {
     // the fused kernel runs on any grid up to the co-resident one
-    const int g = grid > 0 && grid < s.grid_fused ? grid : s.grid_fused;
+    int g = grid > 0 && grid < s.grid_fused ? grid : s.grid_fused;
+    int threads = s.fused_threads;
+    if (s.schedule == 0) {  // shape per solve: one CTA per SM, wider for large graphs
+        threads = m > kAutoWideM ? 1024 : 256;
+        g = s.sms;
+    }
     MST_TRY(begin_solve(s, stream));
     const uint32_t vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)w) & 15u) == 0 ? 1u : 0u;
     if (s.schedule != 2) {
         const uint32_t *wp = (const uint32_t *)w;
         void *args[] = {(void *)&s.ws, (void *)&src, (void *)&dst, (void *)&wp, (void *)&out,
                         (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec};
-        return cudaLaunchCooperativeKernel(fused_kernel(s.fused_threads), dim3(g),
-                                           dim3(s.fused_threads), args, 0, stream);
+        return cudaLaunchCooperativeKernel(fused_kernel(threads), dim3(g), dim3(threads), args,
+                                           0, stream);
     }
     if (!s.exec)
         MST_TRY(build_graph(s));

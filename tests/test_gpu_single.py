@@ -41,7 +41,7 @@ def check(h, n, src, dst, w):
     return got
 
 
-@pytest.fixture(params=[1, 2], ids=["fused", "graph"])
+@pytest.fixture(params=[0, 1, 2], ids=["fused-auto", "fused-fixed", "graph"])
 def sched(request, handle):
     """Runs a test under each single-graph schedule."""
     assert B.mst_set_single_schedule(handle, request.param, 0) == B.MST_OK

@@ -460,21 +460,17 @@ __device__ __forceinline__ void emit_tile(const Ws &ws, Ctl *c, uint32_t tile, u
 }
 
 // Emit of the fused schedule, in two passes with a grid barrier between
-// them instead of a look-back: first every chunk of kEmitWords bit words
-// counts its tree edges (one warp a chunk); then each CTA takes a contiguous
-// range of chunks, sums the counts of all chunks before it, and writes the
-// ids of its chunks in order.
-__device__ __forceinline__ void emit_count(const Ws &ws, uint32_t words, uint32_t nch,
+// them instead of a look-back: first every group of 32 bit words counts its
+// tree edges (one warp a group); then each CTA takes a contiguous range of
+// groups, sums the counts of all groups before it, and its warps write the
+// ids of its groups in order.
+__device__ __forceinline__ void emit_count(const Ws &ws, uint32_t words, uint32_t ngroups,
                                            uint32_t gw, uint32_t nw)
 {
     const int lane = threadIdx.x & 31;
-    for (uint32_t t = gw; t < nch; t += nw) {
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int k = 0; k < kEmitWords / 32; k++) {
-            const uint32_t i = t * kEmitWords + k * 32 + lane;
-            cnt += i < words ? __popc(__ldcg(ws.mst_bits + i)) : 0u;
-        }
+    for (uint32_t t = gw; t < ngroups; t += nw) {
+        const uint32_t i = t * 32 + lane;
+        uint32_t cnt = i < words ? __popc(__ldcg(ws.mst_bits + i)) : 0u;
         cnt = __reduce_add_sync(0xffffffffu, cnt);
         if (lane == 0)
             ws.emit_cnt[t] = cnt;
@@ -536,31 +532,115 @@ __device__ __forceinline__ uint32_t emit_chunk(const Ws &ws, Ctl *c, uint32_t t,
     return total;
 }
 
+// Position of the set bit of rank r (0-based) in w (w has more than r set
+// bits): the smallest p with more than r set bits in w[0..p].
+__device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t r)
+{
+    uint32_t lo = 0, hi = 31;
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)__popc(w & ((2u << mid) - 1u)) > r)  // 2u << 31 wraps to 0: all bits
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// Writes the ids of groups [t0, t1) (this CTA's contiguous range) in
+// ascending order.  The CTA sums the counts of all groups before t0, then
+// takes its range in windows that fit the stage: warp 0 scans a window's
+// counts into shared memory and the warps expand its groups on their own,
+// one group of 32 words each: lane k of an output step finds the word
+// holding the k-th id by a binary search over the warp's scanned counts and
+// the bit by select_bit, so the writes are coalesced.
 template <int kFT>
-__device__ __forceinline__ void emit_range(const Ws &ws, Ctl *c, uint32_t nch, uint32_t words,
+__device__ __forceinline__ void emit_range(const Ws &ws, Ctl *c, uint32_t ngroups, uint32_t words,
                                            uint32_t cap, int32_t *out, TileSmem &sm)
 {
-    const uint32_t per = (nch + gridDim.x - 1) / gridDim.x;
+    constexpr int kFW = kFT / 32;
+    constexpr uint32_t kWindow = sizeof(sm.stage) / 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (ngroups + gridDim.x - 1) / gridDim.x;
     const uint32_t t0 = blockIdx.x * per;
-    const uint32_t t1 = t0 + per < nch ? t0 + per : nch;
+    const uint32_t t1 = t0 + per < ngroups ? t0 + per : ngroups;
     if (t0 >= t1)
         return;
     uint32_t part = 0;
     for (uint32_t t = threadIdx.x; t < t0; t += kFT)
         part += __ldcg(ws.emit_cnt + t);
     part = __reduce_add_sync(0xffffffffu, part);
-    if ((threadIdx.x & 31) == 0)
-        sm.s32[threadIdx.x >> 5] = part;
+    if (lane == 0)
+        sm.s32[warp] = part;
     __syncthreads();
-    uint32_t ex = 0;
+    uint32_t run = 0;  // ids before the current window (kept by every thread)
 #pragma unroll
-    for (int k = 0; k < kFT / 32; k++)
-        ex += sm.s32[k];
-    __syncthreads();
-    for (uint32_t t = t0; t < t1; t++)
-        ex += emit_chunk(ws, c, t, ex, words, cap, out, sm);
-    if (t1 == nch && threadIdx.x == 0)
-        c->emitted = ex;
+    for (int k = 0; k < kFW; k++)
+        run += sm.s32[k];
+    uint32_t *offs = (uint32_t *)sm.stage;  // exclusive offset of each group of the window
+    for (uint32_t w0 = t0; w0 < t1; w0 += kWindow) {
+        const uint32_t w1 = w0 + kWindow < t1 ? w0 + kWindow : t1;
+        __syncthreads();  // the previous window's offsets are no longer read
+        if (warp == 0) {
+            uint32_t r = run;
+            for (uint32_t b = w0; b < w1; b += 32) {
+                const uint32_t t = b + lane;
+                const uint32_t v = t < w1 ? __ldcg(ws.emit_cnt + t) : 0u;
+                uint32_t incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                if (t < w1)
+                    offs[t - w0] = r + incl - v;
+                r += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0)
+                sm.s32[32] = r;
+        }
+        __syncthreads();
+        for (uint32_t t = w0 + warp; t < w1; t += kFW) {
+            const uint32_t base = offs[t - w0];
+            const uint32_t wi = t * 32 + lane;
+            const uint32_t wv = wi < words ? __ldcg(ws.mst_bits + wi) : 0u;
+            const uint32_t cnt = __popc(wv);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            const uint32_t excl = incl - cnt;
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                // the word j holding the id of rank k: the last with excl_j <= k
+                uint32_t j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t e = __shfl_sync(0xffffffffu, excl, (int)(j + step));
+                    if (e <= k)
+                        j += step;
+                }
+                const uint32_t wj = __shfl_sync(0xffffffffu, wv, (int)j);
+                const uint32_t ej = __shfl_sync(0xffffffffu, excl, (int)j);
+                if (k < total) {
+                    const uint32_t id = (t * 32 + j) * 32u + select_bit(wj, k - ej);
+                    if (base + k < cap)
+                        out[base + k] = (int32_t)id;
+                    else
+                        atomicOr(&c->status, ST_INTERNAL);  // more tree edges than n-1
+                }
+            }
+        }
+        run = sm.s32[32];
+    }
+    if (threadIdx.x == 0 && t1 == ngroups)
+        c->emitted = run;
 }
 
 // Final checks of a solve: |M| = n - #components, disconnected flag.
@@ -1072,9 +1152,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             break;
         }
     }
-    // emit: count per chunk, barrier, write
+    // emit: count per group of 32 words, barrier, write
     const uint32_t words = (m + 31u) >> 5;
-    const uint32_t nte = (words + kEmitWords - 1) / kEmitWords;
+    const uint32_t nte = (words + 31u) >> 5;
     const uint32_t cap = n > 0 ? n - 1 : 0;
     emit_count(ws, words, nte, gw, nw);
     grid_sync(ws.bar, gen, status);
@@ -1266,6 +1346,13 @@ static uint32_t desc_capacity(uint32_t n_cap, uint32_t m_cap)
 
 static const int kMaxGridBlocks = 152 * 8 * 2;  // bound for the barrier counters
 
+// Groups of 32 tree-bit words counted by the fused emit.
+static size_t emit_groups(uint32_t m_cap)
+{
+    const size_t words = ((size_t)m_cap + 31) / 32;
+    return (words + 31) / 32 + 1;
+}
+
 // Tail capacities: the pair table covers up to min(kTailMaxN, n) components,
 // and no pair list is longer than the edge list (a pair needs an edge).
 static size_t tail_n_cap(uint32_t n_cap)
@@ -1290,7 +1377,7 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += align_up((((size_t)m_cap + 31) / 32) * 4);
     b += align_up((size_t)m_cap * 8);  // endpoints of possible minima, by id
     b += align_up((size_t)desc_capacity(n_cap, m_cap) * 8);
-    b += align_up((size_t)desc_capacity(n_cap, m_cap) * 4);  // emit chunk counts
+    b += align_up(emit_groups(m_cap) * 4);  // emit group counts
     const size_t tn = tail_n_cap(n_cap), tp = tail_pairs_cap(n_cap, m_cap);
     b += align_up(tn * tn * 8);                  // pair table
     b += 2 * align_up(tp * 16);                  // tail lists
@@ -1454,7 +1541,7 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.eends = (uint2 *)take((size_t)m_cap * 8);
     s.ws.desc_cap = desc_capacity(n_cap, m_cap);
     s.ws.desc = (unsigned long long *)take((size_t)s.ws.desc_cap * 8);
-    s.ws.emit_cnt = (uint32_t *)take((size_t)s.ws.desc_cap * 4);
+    s.ws.emit_cnt = (uint32_t *)take(emit_groups(m_cap) * 4);
     const size_t tn = tail_n_cap(n_cap), tp = tail_pairs_cap(n_cap, m_cap);
     s.ws.pair_tab = (unsigned long long *)take(tn * tn * 8);
     s.ws.tl[0] = (uint4 *)take(tp * 16);

@@ -92,6 +92,12 @@ mst_status mst_destroy(mst_handle h)
     batched_release(h->batched);
     if (h->staging)
         cudaFree(h->staging);
+    for (cudaStream_t cs : h->copy_stream)
+        if (cs)
+            cudaStreamDestroy(cs);
+    for (cudaEvent_t ev : h->copy_event)
+        if (ev)
+            cudaEventDestroy(ev);
     delete h;
     return MST_OK;
 }
@@ -190,9 +196,27 @@ mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m
     int32_t *d_out = (int32_t *)(p + 3 * al(eb));
     int64_t *d_cnt = (int64_t *)(p + 3 * al(eb) + al((size_t)(n > 1 ? n - 1 : 1) * 4));
     if (m > 0) {
-        if (cudaMemcpyAsync(d_src, src, eb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(d_dst, dst, eb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(d_w, w, eb, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        // the three input arrays are copied side by side on three streams
+        // (several copy engines), after the caller's stream and before the solve
+        if (!h->copy_stream[0]) {
+            for (cudaStream_t &cs : h->copy_stream)
+                if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+                    return MST_ERR_CUDA;
+            for (cudaEvent_t &ev : h->copy_event)
+                if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+                    return MST_ERR_CUDA;
+        }
+        cudaStream_t c1 = h->copy_stream[0], c2 = h->copy_stream[1];
+        if (cudaEventRecord(h->copy_event[0], s) != cudaSuccess ||
+            cudaStreamWaitEvent(c1, h->copy_event[0], 0) != cudaSuccess ||
+            cudaStreamWaitEvent(c2, h->copy_event[0], 0) != cudaSuccess ||
+            cudaMemcpyAsync(d_src, src, eb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d_dst, dst, eb, cudaMemcpyHostToDevice, c1) != cudaSuccess ||
+            cudaMemcpyAsync(d_w, w, eb, cudaMemcpyHostToDevice, c2) != cudaSuccess ||
+            cudaEventRecord(h->copy_event[1], c1) != cudaSuccess ||
+            cudaEventRecord(h->copy_event[2], c2) != cudaSuccess ||
+            cudaStreamWaitEvent(s, h->copy_event[1], 0) != cudaSuccess ||
+            cudaStreamWaitEvent(s, h->copy_event[2], 0) != cudaSuccess)
             return MST_ERR_CUDA;
     }
     st = mst_solve_ex(h, wt, n, m, d_src, d_dst, d_w, d_out, d_cnt, stream);

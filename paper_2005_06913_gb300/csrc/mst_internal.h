@@ -156,6 +156,8 @@ struct mst_handle_s {
     LastSolve last_solve;
     void *staging = nullptr;  // device staging of mst_solve_host
     size_t staging_bytes = 0;
+    cudaStream_t copy_stream[2] = {nullptr, nullptr};  // its input copies run side by side
+    cudaEvent_t copy_event[3] = {nullptr, nullptr, nullptr};
     size_t budget = 0;  // 0 = unlimited
     int num_sms = 0;
     mst::Single single;

@@ -129,10 +129,10 @@ __device__ __forceinline__ void find0_range(const Ws &ws, const int32_t *src, co
 
 // Warp tiles: one warp owns a tile of kHookIpl*32 components or kCompIpl*32
 // edges (item j of lane l is tile index j*32 + l, so every load of the warp
-// is contiguous), ranks its items with ballots, takes its offset from the
-// decoupled look-back and writes its results itself.  No block barrier is
-// involved, so a warp waiting on memory or on its predecessor never holds
-// up the other warps of its CTA.
+// is contiguous), ranks its items with ballots, takes a block of ids or
+// positions with one atomicAdd on the round's counter and writes its
+// results itself.  No block barrier and no wait on another warp is
+// involved, so a warp waiting on memory never holds up the others.
 constexpr int kHookIpl = 4, kCompIpl = 8;
 constexpr int kHookWTile = 32 * kHookIpl, kCompWTile = 32 * kCompIpl;
 
@@ -1339,7 +1339,7 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static uint32_t desc_capacity(uint32_t n_cap, uint32_t m_cap)
 {
-    (void)n_cap;  // only emit scans with look-back
+    (void)n_cap;  // only the graph schedule's emit scans with look-back
     const uint32_t words = (m_cap + 31) / 32;
     return (words + kEmitWords - 1) / kEmitWords + 1;
 }

@@ -47,14 +47,23 @@ def workload(cfg: int):
     return g, names[cfg]
 
 
-def kernel_source_sha() -> str:
-    """sha256 prefix of the sources that define the fused single-graph kernel
-    (its tile bodies and device helpers)."""
+def _code_only(text: str) -> str:
+    """C/C++ source without comments, trailing blanks and blank lines (string
+    literals holding comment markers do not occur in these sources)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(l.rstrip() for l in text.splitlines() if l.strip())
+
+
+def kernel_source_sha(src_dir=None) -> str:
+    """sha256 prefix of the code (comments stripped) of the sources that
+    define the fused single-graph kernel: its tile bodies and device helpers."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2005_06913_gb300", "csrc")
+    src = src_dir or os.path.join(ROOT, "paper_2005_06913_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("mst_common.cuh", "mst_single.cu"):
-        h.update(open(os.path.join(src, f), "rb").read())
+        h.update(_code_only(open(os.path.join(src, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -433,18 +433,34 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
     for (uint32_t i = t; i < words; i += T)
         A.bits[i] = 0u;
     tm.sync();
-    // round-0 find-min (Section 2.1, the loop over edges)
-    for (uint32_t e = t; e < m; e += T) {
-        const uint32_t u = (uint32_t)__ldg(src + e), v = (uint32_t)__ldg(dst + e);
-        if (u >= n || v >= n) {
-            atomicOr(status, ST_BAD_VERTEX);
-            continue;
+    // round-0 find-min (Section 2.1, the loop over edges), four edges a
+    // thread per step so that their loads overlap
+    for (uint32_t e0 = t; e0 < m; e0 += 4 * T) {
+        uint32_t us[4], vs[4], xs[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t e = e0 + j * T;
+            const bool in = e < m;
+            us[j] = in ? (uint32_t)__ldg(src + e) : 0u;
+            vs[j] = in ? (uint32_t)__ldg(dst + e) : 0u;
+            xs[j] = in ? __ldg(w + e) : 0u;
         }
-        if (u == v)
-            continue;
-        const unsigned long long key = make_key(weight_bits(__ldg(w + e), wt, status), e);
-        offer_any(&A.mA[u], key);
-        offer_any(&A.mA[v], key);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t e = e0 + j * T;
+            if (e >= m)
+                continue;
+            const uint32_t u = us[j], v = vs[j];
+            if (u >= n || v >= n) {
+                atomicOr(status, ST_BAD_VERTEX);
+                continue;
+            }
+            if (u == v)
+                continue;
+            const unsigned long long key = make_key(weight_bits(xs[j], wt, status), e);
+            offer_any(&A.mA[u], key);
+            offer_any(&A.mA[v], key);
+        }
     }
     tm.sync();
     uint32_t n_r = n, m_r = m;

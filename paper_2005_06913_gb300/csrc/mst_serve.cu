@@ -63,6 +63,8 @@ struct Server {
     std::unordered_map<uint64_t, double> submit_us;
     std::vector<Slot> slots;
     Single lane;  // fused-kernel workspace of the (single) large-request lane
+    std::vector<std::pair<void *, size_t>> retired;  // outgrown lane workspaces, freed at
+                                                     // stop (or when memory runs short)
     int max_batch = 256;
     uint64_t next_ticket = 1;
     size_t in_use = 0;
@@ -148,7 +150,14 @@ static std::vector<Request> take_batch(Server &S, Slot &sl, size_t budget, bool 
                 it = S.pending.erase(it);
                 continue;
             }
-            if (budget && need > have && S.in_use - have + need > budget) {
+            if (budget && need > have && S.in_use + need > budget && !S.retired.empty()) {
+                for (auto &r : S.retired) {  // rare: free outgrown workspaces (waits for the GPU)
+                    cudaFree(r.first);
+                    S.in_use -= r.second;
+                }
+                S.retired.clear();
+            }
+            if (budget && need > have && S.in_use + need > budget) {
                 ++it;  // wait for memory (a medium one goes to a batch instead)
                 continue;
             }
@@ -187,13 +196,28 @@ static cudaError_t launch_big(Server &S, Slot &sl, const Request &r, bool alone)
     const uint32_t n = (uint32_t)r.n, m = (uint32_t)r.m;
     Single &lane = S.lane;
     if (!lane.base || n > lane.ws.n_cap || m > lane.ws.m_cap) {
-        const size_t before = lane.base ? lane.bytes : 0;
+        // The old workspace is kept until the server stops: freeing it now
+        // would wait for every stream of the device, batches included.  The
+        // new one grows geometrically (within the budget), so this happens
+        // a few times per server at most.
+        uint32_t n2 = n, m2 = m;
+        if (lane.base) {
+            S.retired.emplace_back(lane.base, lane.bytes);
+            lane.base = nullptr;
+            n2 = std::max<uint64_t>(n, std::min<uint64_t>(2ull * lane.ws.n_cap, 0x7fffffffu));
+            m2 = std::max<uint64_t>(m, std::min<uint64_t>(2ull * lane.ws.m_cap, 0x7fffffffu));
+            const size_t budget = S.h->budget;
+            if (budget && S.in_use + single_bytes(n2, m2) > budget) {
+                n2 = n;
+                m2 = m;
+            }
+        }
         lane.schedule = 1;  // fixed shape: the grid is chosen per launch below
         lane.fused_blocks_per_sm = 4;
         lane.fused_threads = 256;
-        cudaError_t e = single_reserve(lane, S.h->device, n, m);
+        cudaError_t e = single_reserve(lane, S.h->device, n2, m2);
         std::lock_guard<std::mutex> lk(S.mu);
-        S.in_use = S.in_use - before + (lane.base ? lane.bytes : 0);
+        S.in_use += lane.base ? lane.bytes : 0;
         if (e != cudaSuccess)
             return e;
     }
@@ -424,6 +448,8 @@ mst_status server_stop(mst_handle h)
             cudaFree(sl.d_desc);
     }
     single_release(S->lane);
+    for (auto &r : S->retired)
+        cudaFree(r.first);
     const mst_status st = S->error == cudaSuccess ? MST_OK : MST_ERR_CUDA;
     delete S;
     h->server = nullptr;

@@ -168,7 +168,7 @@ typedef struct {
  * Per-kernel (or per-phase) time and traffic model of the handle's last
  * single-graph solve.  Under the fused schedule (the default) the entries
  * are the phases of the one cooperative kernel (init, find0, hook,
- * compress, compact, emit), timed inside that kernel itself by %globaltimer
+ * compress, compact, tail, emit), timed inside that kernel itself by %globaltimer
  * stamps at each grid barrier; nothing is re-run.  Under the graph schedule
  * the solve is re-run (same device buffers, which must still be valid) with
  * each kernel launched separately between two CUDA events on `stream`, and

@@ -366,6 +366,12 @@ def run_ours(args):
                 "alg_bytes_per_launch": dom_bytes / max(dom_launches, 1),
                 "duration_source": "CUDA events per step (whole solve)" if args.schedule == "fused"
                 else "CUDA-event replay of each kernel"}
+    if args.schedule == "fused":
+        # the gather-inclusive variant: two 4-B label gathers per live edge
+        # per round, which the design keeps in L2
+        gathers = 8.0 * sum(rounds_e[:-1])
+        roofline["alg_bytes_with_gathers_per_launch"] = dom_bytes + gathers
+        roofline["frac_with_gathers"] = (dom_bytes + gathers) / dom_s / 1e9 / hbm_peak
 
     # end to end through the host-buffer C-ABI call, copies inside the timed region
     e2e = None

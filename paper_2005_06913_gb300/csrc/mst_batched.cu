@@ -271,12 +271,17 @@ struct GraphArrays {
 };
 
 // Offers a key to a running minimum that may live in shared or global
-// memory (generic pointer): a filtered atomicMin (values only decrease, so a
-// key not below the current value cannot win).
+// memory (generic pointer): a filtered min (values only decrease, so a key
+// not below the current value cannot win), as a fire-and-forget reduction
+// in global memory and an atomic in shared memory.
 __device__ __forceinline__ void offer_any(unsigned long long *p, unsigned long long key)
 {
-    if (key < *(volatile unsigned long long *)p)
-        atomicMin(p, key);
+    if (key < *(volatile unsigned long long *)p) {
+        if (__isGlobal(p))
+            red_min_u64(p, key);  // fire-and-forget in L2
+        else
+            atomicMin(p, key);
+    }
 }
 
 // Pointer chase with path halving through a volatile view (the array may

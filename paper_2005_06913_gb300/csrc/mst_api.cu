@@ -118,18 +118,14 @@ static mst_status check_graph_args(int32_t n, int64_t m, const int32_t *src, con
     return MST_OK;
 }
 
-mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
-                        const int32_t *src, const int32_t *dst, const void *w,
-                        int32_t *out_edge_ids, int64_t *out_count, void *stream)
+// One single-graph solve (arguments already checked, device set).  With
+// `copy`, src/dst/w are mapped host memory that round 0 reads once while
+// writing the device copy the later phases use.
+static mst_status solve_single(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
+                               const int32_t *src, const int32_t *dst, const void *w,
+                               int32_t *out_edge_ids, int64_t *out_count, cudaStream_t s,
+                               const InputCopy *copy)
 {
-    if (!h || (wt != MST_W_U32 && wt != MST_W_F32))
-        return MST_ERR_INVALID_ARG;
-    mst_status st = check_graph_args(n, m, src, dst, w, out_edge_ids, out_count);
-    if (st != MST_OK)
-        return st;
-    if (cudaSetDevice(h->device) != cudaSuccess)
-        return MST_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
     if (n == 0) {
         // nothing to do: zero edges, status cleared
         h->last = LAST_SINGLE;
@@ -155,9 +151,28 @@ mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
         }
     }
     h->last = LAST_SINGLE;
-    h->last_solve = LastSolve{src, dst, w, out_edge_ids, out_count, nn, mm, (uint32_t)wt, true};
+    if (copy)  // a replay reads the device copy
+        h->last_solve = LastSolve{copy->src, copy->dst, copy->w, out_edge_ids, out_count, nn, mm,
+                                  (uint32_t)wt, true};
+    else
+        h->last_solve = LastSolve{src, dst, w, out_edge_ids, out_count, nn, mm, (uint32_t)wt, true};
     return cuda_status(single_launch(h->single, src, dst, w, (uint32_t)wt, out_edge_ids, out_count,
-                                     nn, mm, s));
+                                     nn, mm, s, 0, copy));
+}
+
+mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
+                        const int32_t *src, const int32_t *dst, const void *w,
+                        int32_t *out_edge_ids, int64_t *out_count, void *stream)
+{
+    if (!h || (wt != MST_W_U32 && wt != MST_W_F32))
+        return MST_ERR_INVALID_ARG;
+    mst_status st = check_graph_args(n, m, src, dst, w, out_edge_ids, out_count);
+    if (st != MST_OK)
+        return st;
+    if (cudaSetDevice(h->device) != cudaSuccess)
+        return MST_ERR_CUDA;
+    return solve_single(h, wt, n, m, src, dst, w, out_edge_ids, out_count, (cudaStream_t)stream,
+                        nullptr);
 }
 
 mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
@@ -195,7 +210,30 @@ mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m
     void *d_w = (void *)(p + 2 * al(eb));
     int32_t *d_out = (int32_t *)(p + 3 * al(eb));
     int64_t *d_cnt = (int64_t *)(p + 3 * al(eb) + al((size_t)(n > 1 ? n - 1 : 1) * 4));
-    if (m > 0) {
+    // Pinned (page-locked, mapped) inputs are read by the fused kernel itself
+    // in round 0, over the host link, while it writes the device copy: no
+    // separate copy pass.  Other host memory is copied in first.
+    const void *mapped[3] = {nullptr, nullptr, nullptr};
+    bool zero_copy = m > 0 && h->single.schedule != 2;
+    const void *hp[3] = {src, dst, w};
+    for (int i = 0; i < 3 && zero_copy; i++) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, hp[i]) != cudaSuccess) {
+            cudaGetLastError();
+            zero_copy = false;
+        } else if (a.type != cudaMemoryTypeHost || !a.devicePointer) {
+            zero_copy = false;
+        } else {
+            mapped[i] = a.devicePointer;
+        }
+    }
+    if (zero_copy) {
+        const InputCopy copy{d_src, d_dst, d_w};
+        st = solve_single(h, wt, n, m, (const int32_t *)mapped[0], (const int32_t *)mapped[1],
+                          mapped[2], d_out, d_cnt, s, &copy);
+        if (st != MST_OK)
+            return st;
+    } else if (m > 0) {
         // the three input arrays are copied side by side on three streams
         // (several copy engines), after the caller's stream and before the solve
         if (!h->copy_stream[0]) {
@@ -219,9 +257,11 @@ mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m
             cudaStreamWaitEvent(s, h->copy_event[2], 0) != cudaSuccess)
             return MST_ERR_CUDA;
     }
-    st = mst_solve_ex(h, wt, n, m, d_src, d_dst, d_w, d_out, d_cnt, stream);
-    if (st != MST_OK)
-        return st;
+    if (!zero_copy) {
+        st = mst_solve_ex(h, wt, n, m, d_src, d_dst, d_w, d_out, d_cnt, stream);
+        if (st != MST_OK)
+            return st;
+    }
     if (n > 1 && cudaMemcpyAsync(out_edge_ids, d_out, (size_t)(n - 1) * 4, cudaMemcpyDeviceToHost,
                                  s) != cudaSuccess)
         return MST_ERR_CUDA;

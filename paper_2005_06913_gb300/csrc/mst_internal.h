@@ -51,9 +51,17 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap);
 cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m);
 void single_release(Single &s);
 // Queues one solve on `stream` (arguments already validated).
+// Device copy of a solve's inputs that the fused kernel writes while its
+// round-0 find-min reads them from mapped host memory.
+struct InputCopy {
+    int32_t *src;
+    int32_t *dst;
+    void *w;
+};
+
 cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n,
-                          uint32_t m, cudaStream_t stream, int grid = 0);
+                          uint32_t m, cudaStream_t stream, int grid = 0, const InputCopy *copy = nullptr);
 double single_alg_bytes(const Ctl &c);
 // Per-phase times of the last fused solve (its own phase log; synchronous).
 cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<KernelProfile> &prof);

@@ -90,11 +90,33 @@ __device__ __forceinline__ void load4_soa(const int32_t *__restrict__ src,
     }
 }
 
+// Writes one group of 4 edges' fields to the device copy of the inputs
+// (128-bit stores; the copy is 256-byte aligned and groups start at 4k).
+__device__ __forceinline__ void store4_soa(int32_t *csrc, int32_t *cdst, uint32_t *cw, uint32_t e0,
+                                           uint32_t m, const int32_t (&us)[4],
+                                           const int32_t (&vs)[4], const uint32_t (&wr)[4])
+{
+    if (e0 + 3 < m) {
+        *(int4 *)(csrc + e0) = make_int4(us[0], us[1], us[2], us[3]);
+        *(int4 *)(cdst + e0) = make_int4(vs[0], vs[1], vs[2], vs[3]);
+        *(uint4 *)(cw + e0) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+    } else {
+        for (int j = 0; j < 4 && e0 + j < m; j++) {
+            csrc[e0 + j] = us[j];
+            cdst[e0 + j] = vs[j];
+            cw[e0 + j] = wr[j];
+        }
+    }
+}
+
 // Round-0 find-min over edge groups [g0, groups) step gstep (4 edges each).
+// With csrc non-null the inputs are read from mapped host memory and also
+// copied to device memory (csrc, cdst, cw), which the later phases read.
 __device__ __forceinline__ void find0_range(const Ws &ws, const int32_t *src, const int32_t *dst,
                                             const uint32_t *w, uint32_t n, uint32_t m, uint32_t wt,
                                             uint32_t vec, uint32_t *status, size_t g0,
-                                            size_t gstep)
+                                            size_t gstep, int32_t *csrc = nullptr,
+                                            int32_t *cdst = nullptr, uint32_t *cw = nullptr)
 {
     unsigned long long *mn = ws.mins[0];
     const size_t groups = ((size_t)m + 3) >> 2;
@@ -104,6 +126,8 @@ __device__ __forceinline__ void find0_range(const Ws &ws, const int32_t *src, co
         int32_t us[4], vs[4];
         uint32_t wr[4];
         load4_soa(src, dst, w, e0, m, vec, us, vs, wr);
+        if (csrc)
+            store4_soa(csrc, cdst, cw, e0, m, us, vs, wr);
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             if (e0 + j >= m)
@@ -1021,7 +1045,8 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
 template <int kFT>
 __global__ void __launch_bounds__(kFT, 1024 / kFT)
 k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_t *out,
-        int64_t *out_count, uint32_t n, uint32_t m, uint32_t wt, uint32_t vec)
+        int64_t *out_count, uint32_t n, uint32_t m, uint32_t wt, uint32_t vec, int32_t *csrc,
+        int32_t *cdst, uint32_t *cw)
 {
     constexpr int kFW = kFT / 32;
     __shared__ TileSmem sm;
@@ -1047,10 +1072,15 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
     }
     grid_sync(ws.bar, gen, status);
     log_phase(c, PH_INIT);
-    find0_range(ws, src, dst, w, n, m, wt, vec, status, gtid, gstride);
+    find0_range(ws, src, dst, w, n, m, wt, vec, status, gtid, gstride, csrc, cdst, cw);
     mark_work(c);
     grid_sync(ws.bar, gen, status);
     log_phase(c, PH_FIND0);
+    if (csrc) {  // host inputs: the later phases read the device copy
+        src = csrc;
+        dst = cdst;
+        w = cw;
+    }
     uint32_t n_cur = n, m_cur = m, r = 0;
     for (;; r++) {
         // hook + new ids of the roots
@@ -1591,7 +1621,7 @@ static cudaError_t begin_solve(Single &s, cudaStream_t stream)
 
 cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n, uint32_t m,
-                          cudaStream_t stream, int grid)
+                          cudaStream_t stream, int grid, const InputCopy *copy)
 {
     // the fused kernel runs on any grid up to the co-resident one
     int g = grid > 0 && grid < s.grid_fused ? grid : s.grid_fused;
@@ -1604,8 +1634,11 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
     const uint32_t vec = (((uintptr_t)src | (uintptr_t)dst | (uintptr_t)w) & 15u) == 0 ? 1u : 0u;
     if (s.schedule != 2) {
         const uint32_t *wp = (const uint32_t *)w;
+        int32_t *csrc = copy ? copy->src : nullptr, *cdst = copy ? copy->dst : nullptr;
+        uint32_t *cw = copy ? (uint32_t *)copy->w : nullptr;
         void *args[] = {(void *)&s.ws, (void *)&src, (void *)&dst, (void *)&wp, (void *)&out,
-                        (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec};
+                        (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec,
+                        (void *)&csrc, (void *)&cdst, (void *)&cw};
         return cudaLaunchCooperativeKernel(fused_kernel(threads), dim3(g), dim3(threads), args,
                                            0, stream);
     }

@@ -266,14 +266,36 @@ def test_async_on_side_stream(handle):
     assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w))
 
 
-def test_host_buffer_solve(handle):
-    g = gg.random_connected(20000, 80000, 17)
-    hs, hd = torch.from_numpy(g.src), torch.from_numpy(g.dst)
-    hw = torch.from_numpy(g.w.view(np.int32))
-    ho = torch.full((g.n - 1,), -1, dtype=torch.int32)
-    hc = torch.zeros(1, dtype=torch.int64)
-    st = B.mst_solve_host(handle, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc)
-    assert st == B.MST_OK
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "pinned"])
+@pytest.mark.parametrize("shape", [(20000, 80000, 17), (1024, 1024 * 3 + 1, 5), (300000, 900001, 9)])
+def test_host_buffer_solve(sched, pinned, shape):
+    """Host inputs: pageable memory is copied in first; pinned memory is read
+    by the fused kernel in round 0 while it writes the device copy (the graph
+    schedule copies it in).  Odd m exercises the ragged last group."""
+    n, m, seed = shape
+    g = gg.random_connected(n, m, seed)
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    hs, hd = pin(torch.from_numpy(g.src)), pin(torch.from_numpy(g.dst))
+    hw = pin(torch.from_numpy(g.w.view(np.int32)))
+    ho = pin(torch.full((g.n - 1,), -1, dtype=torch.int32))
+    hc = pin(torch.zeros(1, dtype=torch.int64))
+    ref = oracle.kruskal(g.n, g.src, g.dst, g.w)
+    for _ in range(2):  # twice: the second solve reuses the staging and the copy
+        st = B.mst_solve_host(sched, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc)
+        assert st == B.MST_OK
+        assert np.array_equal(ho[: int(hc.item())].numpy(), ref)
+
+
+def test_host_buffer_then_replay(handle):
+    """A profile replay after a pinned host-buffer solve reads the device copy."""
+    g = gg.random_connected(30000, 120000, 31)
+    hs, hd = torch.from_numpy(g.src).pin_memory(), torch.from_numpy(g.dst).pin_memory()
+    hw = torch.from_numpy(g.w.view(np.int32)).pin_memory()
+    ho = torch.full((g.n - 1,), -1, dtype=torch.int32).pin_memory()
+    hc = torch.zeros(1, dtype=torch.int64).pin_memory()
+    assert B.mst_solve_host(handle, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc) == B.MST_OK
+    prof = B.mst_profile_last_solve(handle)
+    assert any(p["name"].startswith("k_solve:find0") for p in prof)
     assert np.array_equal(ho[: int(hc.item())].numpy(), oracle.kruskal(g.n, g.src, g.dst, g.w))
 
 

@@ -106,12 +106,16 @@ mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
                         int32_t *out_edge_ids, int64_t *out_count, void *stream);
 
 /*
- * Host-buffer form of mst_solve_ex for callers whose graph is in host memory:
- * copies src, dst and w (host pointers; page-locked memory copies fastest)
- * into device staging owned by the handle, solves, copies the tree's edge
- * ids (host int32 capacity >= max(n-1,0)) and *out_count (host int64) back,
- * and returns after the result is in host memory (synchronises `stream`).
- * Returns an argument error, or else the device status as mst_get_status.
+ * Host-buffer form of mst_solve_ex for callers whose graph is in host memory
+ * (src, dst, w are host pointers).  If all three are page-locked (pinned)
+ * and the fused schedule is selected, the kernel reads them itself in round
+ * 0 over the host link and writes their device copy into staging owned by
+ * the handle; otherwise they are first copied into that staging.  Then the
+ * tree's edge ids (host int32 capacity >= max(n-1,0)) and *out_count (host
+ * int64) are copied back, and the call returns after the result is in host
+ * memory (synchronises `stream`).  The host inputs must not change until the
+ * call returns.  Returns an argument error, or else the device status as
+ * mst_get_status.
  */
 mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
                           const int32_t *src, const int32_t *dst, const void *w,

@@ -110,10 +110,11 @@ mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
  * (src, dst, w are host pointers).  If all three are page-locked (pinned)
  * and the fused schedule is selected, the kernel reads them itself in round
  * 0 over the host link and writes their device copy into staging owned by
- * the handle; otherwise they are first copied into that staging.  Then the
+ * the handle; otherwise they are first copied into that staging.  The
  * tree's edge ids (host int32 capacity >= max(n-1,0)) and *out_count (host
- * int64) are copied back, and the call returns after the result is in host
- * memory (synchronises `stream`).  The host inputs must not change until the
+ * int64) are written by the kernel itself when they too are pinned (and the
+ * inputs are), else copied back; the call returns after the result is in
+ * host memory (synchronises `stream`).  The host inputs must not change until the
  * call returns.  Returns an argument error, or else the device status as
  * mst_get_status.
  */

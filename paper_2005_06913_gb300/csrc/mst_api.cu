@@ -227,12 +227,31 @@ mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m
             mapped[i] = a.devicePointer;
         }
     }
+    // pinned outputs are written by the kernel itself (no copy back)
+    void *out_mapped[2] = {nullptr, nullptr};
+    bool direct_out = zero_copy;
+    void *op[2] = {out_edge_ids, out_count};
+    for (int i = 0; i < 2 && direct_out; i++) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, op[i]) != cudaSuccess) {
+            cudaGetLastError();
+            direct_out = false;
+        } else if (a.type != cudaMemoryTypeHost || !a.devicePointer) {
+            direct_out = false;
+        } else {
+            out_mapped[i] = a.devicePointer;
+        }
+    }
     if (zero_copy) {
         const InputCopy copy{d_src, d_dst, d_w};
+        int32_t *o = direct_out ? (int32_t *)out_mapped[0] : d_out;
+        int64_t *oc = direct_out ? (int64_t *)out_mapped[1] : d_cnt;
         st = solve_single(h, wt, n, m, (const int32_t *)mapped[0], (const int32_t *)mapped[1],
-                          mapped[2], d_out, d_cnt, s, &copy);
+                          mapped[2], o, oc, s, &copy);
         if (st != MST_OK)
             return st;
+        if (direct_out)
+            return mst_get_status(h, stream);
     } else if (m > 0) {
         // the three input arrays are copied side by side on three streams
         // (several copy engines), after the caller's stream and before the solve

@@ -266,19 +266,21 @@ def test_async_on_side_stream(handle):
     assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w))
 
 
-@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "pinned"])
+@pytest.mark.parametrize("pinned", ["none", "inputs", "all"])
 @pytest.mark.parametrize("shape", [(20000, 80000, 17), (1024, 1024 * 3 + 1, 5), (300000, 900001, 9)])
 def test_host_buffer_solve(sched, pinned, shape):
-    """Host inputs: pageable memory is copied in first; pinned memory is read
-    by the fused kernel in round 0 while it writes the device copy (the graph
-    schedule copies it in).  Odd m exercises the ragged last group."""
+    """Host buffers: pageable inputs are copied in first; pinned inputs are
+    read by the fused kernel in round 0 while it writes the device copy (the
+    graph schedule copies them in); pinned outputs are written by the kernel
+    directly.  Odd m exercises the ragged last group."""
     n, m, seed = shape
     g = gg.random_connected(n, m, seed)
-    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
-    hs, hd = pin(torch.from_numpy(g.src)), pin(torch.from_numpy(g.dst))
-    hw = pin(torch.from_numpy(g.w.view(np.int32)))
-    ho = pin(torch.full((g.n - 1,), -1, dtype=torch.int32))
-    hc = pin(torch.zeros(1, dtype=torch.int64))
+    pin_in = (lambda t: t.pin_memory()) if pinned != "none" else (lambda t: t)
+    pin_out = (lambda t: t.pin_memory()) if pinned == "all" else (lambda t: t)
+    hs, hd = pin_in(torch.from_numpy(g.src)), pin_in(torch.from_numpy(g.dst))
+    hw = pin_in(torch.from_numpy(g.w.view(np.int32)))
+    ho = pin_out(torch.full((g.n - 1,), -1, dtype=torch.int32))
+    hc = pin_out(torch.zeros(1, dtype=torch.int64))
     ref = oracle.kruskal(g.n, g.src, g.dst, g.w)
     for _ in range(2):  # twice: the second solve reuses the staging and the copy
         st = B.mst_solve_host(sched, B.MST_W_U32, g.n, g.m, hs, hd, hw, ho, hc)

@@ -20,9 +20,7 @@ namespace mst {
 
 constexpr int kThreads = 256;                 // threads per block, streaming kernels
 constexpr int kWarps = kThreads / 32;         // 8
-constexpr int kItems = 4;                     // items per thread per tile
-constexpr int kTile = kThreads * kItems;      // 1024 items per tile
-static_assert(kItems * kWarps == 32, "tile ranking scans 32 (row, warp) counts in one warp");
+constexpr int kTile = 1024;                   // 16-byte slots of a CTA's shared stage
 constexpr int kMaxRounds = 64;                // > log2(2^31) + 1: never reached
 constexpr uint64_t kNoEdge = ~0ull;           // minimum[] = -1 of Section 2.1
 constexpr int kChaseLimit = 64;               // pointer hops per thread per pass
@@ -203,88 +201,6 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// ------------------------------------------------------------ tile ranking
-
-// Striped tile layout: item j of thread t is tile index j*kThreads + t, so
-// every load instruction of a warp is contiguous.  Given keep flags, returns
-// each kept item's rank among the tile's kept items in index order (stable)
-// and the tile's total.  s32 is 33 words of shared memory.
-__device__ __forceinline__ void tile_ranks_striped(const bool (&keep)[kItems],
-                                                   uint32_t (&rank)[kItems],
-                                                   uint32_t &total, uint32_t *s32)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t mask[kItems];
-#pragma unroll
-    for (int j = 0; j < kItems; j++)
-        mask[j] = __ballot_sync(0xffffffffu, keep[j]);
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < kItems; j++)
-            s32[j * kWarps + warp] = __popc(mask[j]);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t v = s32[lane], incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o)
-                incl += y;
-        }
-        s32[lane] = incl - v;
-        if (lane == 31)
-            s32[32] = incl;
-    }
-    __syncthreads();
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int j = 0; j < kItems; j++)
-        rank[j] = s32[j * kWarps + warp] + __popc(mask[j] & lt);
-    total = s32[32];
-}
-
-// Blocked tile layout: items j of thread t are tile indices 4t .. 4t+3 (one
-// 128-bit load per array).  Same contract as tile_ranks_striped.
-__device__ __forceinline__ void tile_ranks_blocked(const bool (&keep)[kItems],
-                                                   uint32_t (&rank)[kItems],
-                                                   uint32_t &total, uint32_t *s32)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt = lanemask_lt();
-    uint32_t before = 0, wcount = 0;
-#pragma unroll
-    for (int j = 0; j < kItems; j++) {
-        uint32_t mk = __ballot_sync(0xffffffffu, keep[j]);
-        before += __popc(mk & lt);
-        wcount += __popc(mk);
-    }
-    if (lane == 0)
-        s32[warp] = wcount;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t v = lane < kWarps ? s32[lane] : 0, incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o)
-                incl += y;
-        }
-        if (lane < kWarps)
-            s32[lane] = incl - v;
-        if (lane == 31)
-            s32[32] = incl;
-    }
-    __syncthreads();
-    uint32_t run = s32[warp] + before;
-#pragma unroll
-    for (int j = 0; j < kItems; j++) {
-        rank[j] = run;
-        run += keep[j] ? 1u : 0u;
-    }
-    total = s32[32];
 }
 
 // ------------------------------------------------- decoupled look-back scan

@@ -501,61 +501,6 @@ __device__ __forceinline__ void emit_count(const Ws &ws, uint32_t words, uint32_
     }
 }
 
-// Writes the ids of chunk t at out[ex...] (ascending); returns its count.
-__device__ __forceinline__ uint32_t emit_chunk(const Ws &ws, Ctl *c, uint32_t t, uint32_t ex,
-                                               uint32_t words, uint32_t cap, int32_t *out,
-                                               TileSmem &sm)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (int)(blockDim.x >> 5);
-    const uint32_t i = t * kEmitWords + threadIdx.x;
-    const uint32_t wv = (threadIdx.x < kEmitWords && i < words) ? __ldcg(ws.mst_bits + i) : 0u;
-    const uint32_t cnt = __popc(wv);
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o)
-            incl += y;
-    }
-    if (lane == 31)
-        sm.s32[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t v = lane < nwarps ? sm.s32[lane] : 0u;
-        uint32_t inc2 = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc2, o);
-            if (lane >= o)
-                inc2 += y;
-        }
-        if (lane < nwarps)
-            sm.s32[lane] = inc2 - v;
-        if (lane == 31)
-            sm.s32[32] = inc2;
-    }
-    __syncthreads();
-    const uint32_t total = sm.s32[32];
-    uint32_t pos = sm.s32[warp] + incl - cnt;
-    uint32_t *ids = (uint32_t *)sm.stage;
-    uint32_t bits = wv;
-    while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        ids[pos++] = i * 32u + (uint32_t)b;
-    }
-    __syncthreads();
-    for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
-        if (ex + k < cap)
-            out[ex + k] = (int32_t)ids[k];
-        else
-            atomicOr(&c->status, ST_INTERNAL);  // more tree edges than n-1
-    }
-    __syncthreads();
-    return total;
-}
-
 // Position of the set bit of rank r (0-based) in w (w has more than r set
 // bits): the smallest p with more than r set bits in w[0..p].
 __device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t r)

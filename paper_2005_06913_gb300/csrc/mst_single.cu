@@ -831,7 +831,7 @@ __device__ __forceinline__ void extract_pairs(const Ws &ws, Ctl *c, uint32_t n_t
 // Every CTA of the grid enters; CTAs outside a round's team leave.  CTA 0
 // always stays and records the components left in c->tail_added.
 constexpr int kTailU = 4;
-constexpr uint32_t kTailEdgesPerThread = 8;
+constexpr uint32_t kTailEdgesPerThread = 4;  // swept 2..64: 4 is fastest on small graphs
 
 template <int kFT>
 __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, uint32_t r_base,

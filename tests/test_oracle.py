@@ -357,3 +357,29 @@ def test_total_weight_lower_bound(oracle_mod):
     for g in (gg.config(1), gg.grid2d(50, 50, 2)):
         t = oracle_mod.kruskal(g.n, g.src, g.dst, g.w)
         assert oracle_mod.total_weight(g.w, t) >= g.n * (g.n - 1) // 2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_parallel_edges_reduce_to_lightest(oracle_mod, seed):
+    """Reading 7 (used when few components remain): of parallel edges between
+    the same two vertices only the lightest under (weight, id) can be in the
+    tree, so the tree of a multigraph equals the tree of its reduction to
+    one edge per vertex pair.  Heavy ties make the id tie-break matter."""
+    rng = np.random.default_rng(900 + seed)
+    n = 30
+    m = 400
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    w = rng.integers(1, 6, m).astype(np.uint32)
+    full = set(oracle_mod.kruskal(n, src, dst, w).tolist())
+    best = {}
+    for e in range(m):
+        a, b = int(src[e]), int(dst[e])
+        if a == b:
+            continue
+        pair = (min(a, b), max(a, b))
+        if pair not in best or (int(w[e]), e) < (int(w[best[pair]]), best[pair]):
+            best[pair] = e
+    keep = np.array(sorted(best.values()), dtype=np.int64)
+    reduced = oracle_mod.kruskal(n, src[keep], dst[keep], w[keep])
+    assert full == set(keep[reduced].tolist())

@@ -11,6 +11,7 @@ the timed events.
                   [--config 1|2|3] [--no-cpu-baseline] [--schedule fused|graph]
   python bench.py --workload batched [--graphs G]     # C4: G graphs in one launch
   python bench.py --workload serving [--pool P] [--rates 1000,5000] [--seconds S]
+  python bench.py --workload paper-cpu   (the paper's sequential comparison, host only)
 
 Under torchrun (N > 1) every rank solves its own replica of the workload (a
 single solve does not shard); value = edges of all ranks / max rank time.
@@ -685,6 +686,46 @@ def run_serving(args):
     return 0
 
 
+PAPER_TABLE1 = ["Graph10K_3", "Graph10K_6", "Graph10K_9", "Graph100K_3", "Graph100K_6",
+                "Graph100K_9", "Graph1M_3", "Graph1M_6", "Graph1M_9"]
+
+
+def run_paper_cpu(args):
+    """The paper's sequential comparison (Section 2.1 "Optimization", Fig. 1:
+    the covered-edge optimisation makes sequential Boruvka 24-45% faster) on
+    the Table 1 shapes, with the oracle on this host's cores, one thread:
+    sequential Boruvka without and with the optimisation, and Kruskal; the
+    median of 3 runs each.  No GPU work."""
+    import oracle
+    from paper_2005_06913_gb300 import graphgen as gg
+
+    oracle.build()
+    rows = []
+    for name in PAPER_TABLE1:
+        g = gg.paper_table1(name)
+        runs = {"boruvka_plain": lambda: oracle.boruvka(g.n, g.src, g.dst, g.w, covered=False),
+                "boruvka_covered": lambda: oracle.boruvka(g.n, g.src, g.dst, g.w, covered=True),
+                "kruskal": lambda: oracle.kruskal(g.n, g.src, g.dst, g.w)}
+        row = {"graph": name, "n": g.n, "m": g.m}
+        for label, fn in runs.items():
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                fn()
+                ts.append(time.perf_counter() - t0)
+            row[label + "_ms"] = round(statistics.median(ts) * 1e3, 2)
+        plain, cov = row["boruvka_plain_ms"], row["boruvka_covered_ms"]
+        row["covered_time_saved_pct"] = round(100.0 * (plain - cov) / plain, 1)
+        rows.append(row)
+    print(json.dumps({"metric": "sequential Boruvka time without and with the covered-edge "
+                                "optimisation, and Kruskal (oracle, one host thread)",
+                      "impl": "oracle", "unit": "ms", "cores": 1, "data": "synthetic",
+                      "config": {"workload": "the paper's Table 1 shapes (random connected, "
+                                             "n in 10K/100K/1M, degree 3/6/9)"},
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -696,7 +737,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", choices=["fused", "graph"], default="fused")
-    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
+    ap.add_argument("--workload", choices=["single", "batched", "serving", "paper-cpu"],
+                    default="single")
     ap.add_argument("--graphs", type=int, default=4096)
     ap.add_argument("--per-graph-sample", type=int, default=256)
     ap.add_argument("--pool", type=int, default=128)
@@ -714,6 +756,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "paper-cpu":
+        return run_paper_cpu(args)
     return run_ours(args)
 
 

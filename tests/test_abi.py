@@ -31,6 +31,29 @@ def test_null_handle_rejected_on_host(lib_built):
     assert L.mst_create(None, 0, 0) == B.MST_ERR_INVALID_ARG
 
 
+def test_every_handle_entry_point_rejects_null(lib_built):
+    """Each entry point taking a handle checks it on the host, before any
+    CUDA call (so this runs without a GPU)."""
+    L = B.lib()
+    bad = B.MST_ERR_INVALID_ARG
+    tk = ctypes.c_uint64(0)
+    done = ctypes.c_int(0)
+    cnt = ctypes.c_int32(0)
+    assert L.mst_solve_host(None, 0, 4, 3, None, None, None, None, None, None) == bad
+    assert L.mst_solve_batched(None, 0, 1, None, None, 4, 3, None, None, None, None, None,
+                               None) == bad
+    assert L.mst_autotune_batched(None, 0, 1, None, None, 4, 3, None, None, None, None, None,
+                                  None, None) == bad
+    assert L.mst_set_single_schedule(None, 0, 0, 0) == bad
+    assert L.mst_profile_last_solve(None, None, None, 0, ctypes.byref(cnt)) == bad
+    assert L.mst_get_round_stats(None, None, None, None, 0, ctypes.byref(cnt)) == bad
+    assert L.mst_server_start(None, 2, 4) == bad
+    assert L.mst_submit(None, 0, 4, 3, None, None, None, None, None, ctypes.byref(tk)) == bad
+    assert L.mst_poll(None, 1, ctypes.byref(done), None) == bad
+    assert L.mst_server_drain(None) == bad
+    assert L.mst_server_stop(None) == bad
+
+
 def test_create_bad_device(lib_built):
     h = ctypes.c_void_p()
     assert B.lib().mst_create(ctypes.byref(h), -1, 0) == B.MST_ERR_INVALID_ARG

@@ -8,7 +8,7 @@ emit) with the inputs already resident in HBM.  The 25 MB input fits in the
 the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config 1|2|3] [--no-cpu-baseline] [--schedule fused|graph]
+                  [--config 1|2|3] [--no-cpu-baseline] [--schedule fused|graph|covered]
   python bench.py --workload batched [--graphs G]     # C4: G graphs in one launch
   python bench.py --workload serving [--pool P] [--rates 1000,5000] [--seconds S]
   python bench.py --workload paper-cpu   (the paper's sequential comparison, host only)
@@ -297,7 +297,8 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     h = B.mst_create(dev, 0)
-    B.mst_set_single_schedule(h, 0 if args.schedule == "fused" else 2, 0, 0)
+    fused = args.schedule in ("fused", "covered")
+    B.mst_set_single_schedule(h, {"fused": 0, "graph": 2, "covered": 3}[args.schedule], 0, 0)
 
     def solve():
         st = B.mst_solve(h, g.n, g.m, src, dst, w, out, cnt, stream)
@@ -353,7 +354,7 @@ def run_ours(args):
     kernels = [{"name": full(p["name"]), "count": p["launches"], "ms": round(p["total_ms"], 4),
                 "alg_MB": round(p["alg_bytes"] / 1e6, 3),
                 "GBps": round(p["alg_bytes"] / max(p["total_ms"], 1e-9) / 1e6, 1)} for p in prof]
-    if args.schedule == "fused":
+    if fused:
         launches_per_step = 1
         dom_name, dom_bytes, dom_s, dom_launches = "k_solve", solve_bytes, step_s, 1
     else:
@@ -364,13 +365,15 @@ def run_ours(args):
     achieved = dom_bytes / dom_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic_for(dom_name, TRAFFIC_WORKLOAD.get(args.config)),
+                # counters were taken under the default schedule only
+                "traffic": traffic_for(dom_name, TRAFFIC_WORKLOAD.get(args.config))
+                if args.schedule == "fused" else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",
                 "launches_per_step": dom_launches,
                 "alg_bytes_per_launch": dom_bytes / max(dom_launches, 1),
-                "duration_source": "CUDA events per step (whole solve)" if args.schedule == "fused"
+                "duration_source": "CUDA events per step (whole solve)" if fused
                 else "CUDA-event replay of each kernel"}
-    if args.schedule == "fused":
+    if fused:
         # the gather-inclusive variant: two 4-B label gathers per live edge
         # per round, which the design keeps in L2
         gathers = 8.0 * sum(rounds_e[:-1])
@@ -391,9 +394,10 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)"
                          if not args.no_flush else "not flushed",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "schedule": args.schedule,
                    "timer": "CUDA events per step on the launching stream"},
         "roofline": roofline,
-        "phases" if args.schedule == "fused" else "kernel_replay": kernels,
+        "phases" if fused else "kernel_replay": kernels,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -736,7 +740,9 @@ def main():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--schedule", choices=["fused", "graph"], default="fused")
+    # covered: the ablation that flags internal edges in place instead of
+    # compacting the list (the sequential optimisation of Section 2.1)
+    ap.add_argument("--schedule", choices=["fused", "graph", "covered"], default="fused")
     ap.add_argument("--workload", choices=["single", "batched", "serving", "paper-cpu"],
                     default="single")
     ap.add_argument("--graphs", type=int, default=4096)

@@ -194,8 +194,11 @@ mst_status mst_profile_last_solve(mst_handle h, void *stream, mst_kernel_profile
  * size and blocks_per_sm (1..8, 0 = keep, default 4) the CTAs per SM, clamped
  * to what fits (64 registers a thread: 1024 threads a CTA fit once per SM,
  * 256 four times); 2 = one kernel per phase replayed from a CUDA graph whose
- * round loop is a device-side conditional WHILE node.  Results are identical
- * under every setting.
+ * round loop is a device-side conditional WHILE node; 3 = an ablation of
+ * schedule 0 after the sequential "covered" optimisation (Section 2.1): the
+ * edge list is never compacted, every round reads all m slots and edges that
+ * became internal are flagged in their slot and skipped.  Results are
+ * identical under every setting.
  */
 mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm,
                                    int block_threads);

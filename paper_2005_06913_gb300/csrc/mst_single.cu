@@ -331,21 +331,36 @@ __device__ __forceinline__ bool compress_range(const Ws &ws, uint32_t n_cur, boo
     return unfinished;
 }
 
+// The "covered" ablation (the sequential optimisation of Section 2.1 kept
+// on the GPU as a flag): the list keeps all m slots in E[1] and a slot whose
+// edge has become internal is overwritten by this marker, whose first
+// endpoint is never a component id; later rounds read and skip it.
+constexpr uint32_t kDeadEdge = 0xffffffffu;
+
+__device__ __forceinline__ uint4 *edge_list(const Ws &ws, uint32_t round, bool covered, bool next)
+{
+    if (covered)
+        return ws.E[1];
+    return ((round & 1) != 0) != next ? ws.E[1] : ws.E[0];
+}
+
 // Compaction of one warp tile of round r's live edges fused with find-min
 // of round r+1: survivors are written from registers to a block of
 // positions taken from the round's counter (one contiguous run per row of
 // the tile), possible minima record their new endpoints by input id, and
-// they offer their (weight, id) keys with fire-and-forget reductions.
-template <bool R0>
+// they offer their (weight, id) keys with fire-and-forget reductions.  In
+// the covered ablation survivors are rewritten in their own slot and newly
+// internal edges are flagged there instead.
+template <bool R0, bool covered = false>
 __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t tile,
                                               uint32_t round, uint32_t m_cur, uint32_t n_next,
                                               uint32_t n_in,
                                               uint32_t wt, const int32_t *src, const int32_t *dst,
-                                              const uint32_t *w)
+                                              const uint32_t *w, uint32_t m_live = 0)
 {
     const int lane = threadIdx.x & 31;
-    const uint4 *ecur = (round & 1) ? ws.E[1] : ws.E[0];
-    uint4 *enext = (round & 1) ? ws.E[0] : ws.E[1];
+    const uint4 *ecur = edge_list(ws, round, covered, false);
+    uint4 *enext = edge_list(ws, round, covered, true);
     unsigned long long *mnext = (round & 1) ? ws.mins[0] : ws.mins[1];
     const int32_t *__restrict__ lab = ws.lab;
     uint32_t *status = &c->status;
@@ -364,7 +379,7 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
             rec[j] = make_uint4(u, v, x, i);
         } else {
             rec[j] = in ? ecur[i] : make_uint4(0, 0, 0, 0);
-            ok[j] = in;
+            ok[j] = in && rec[j].x != kDeadEdge;
         }
     }
     uint32_t mask[kCompIpl], total = 0;
@@ -391,12 +406,16 @@ __device__ __forceinline__ void compact_wtile(const Ws &ws, Ctl *c, uint32_t til
         ex = atomicAdd(&c->cnt_m[round], total);
     ex = __shfl_sync(0xffffffffu, ex, 0);
     const uint32_t lt = lanemask_lt();
-    const bool filtered = use_filter(m_cur, n_next);
+    const bool filtered = use_filter(covered ? m_live : m_cur, n_next);
     uint32_t run = ex;
 #pragma unroll
     for (int j = 0; j < kCompIpl; j++) {
+        const uint32_t i = base + j * 32 + lane;
+        // flagged, not removed: every slot of round 0, later only new ones
+        if (covered && !((mask[j] >> lane) & 1u) && (R0 ? i < m_cur : ok[j]))
+            enext[i] = make_uint4(kDeadEdge, kDeadEdge, 0u, 0u);
         if ((mask[j] >> lane) & 1u) {
-            const uint32_t pos = run + __popc(mask[j] & lt);
+            const uint32_t pos = covered ? i : run + __popc(mask[j] & lt);
             enext[pos] = rec[j];
             const unsigned long long key = make_key(rec[j].z, rec[j].w);
             // Only an edge that passes a filter can end up as a minimum (the
@@ -761,10 +780,10 @@ __device__ __forceinline__ void compact_pairs_wtile(const Ws &ws, Ctl *c, uint32
                                                     uint32_t round, uint32_t m_cur,
                                                     uint32_t n_next, uint32_t n_in, uint32_t wt,
                                                     const int32_t *src, const int32_t *dst,
-                                                    const uint32_t *w)
+                                                    const uint32_t *w, bool covered)
 {
     const int lane = threadIdx.x & 31;
-    const uint4 *ecur = (round & 1) ? ws.E[1] : ws.E[0];
+    const uint4 *ecur = edge_list(ws, round, covered, false);
     const int32_t *lab = ws.lab;
     uint32_t *status = &c->status;
     const uint32_t base = tile * kCompWTile;
@@ -780,7 +799,7 @@ __device__ __forceinline__ void compact_pairs_wtile(const Ws &ws, Ctl *c, uint32
             ok = rec.x < n_in && rec.y < n_in && rec.x != rec.y;
         } else {
             rec = ecur[i];
-            ok = true;
+            ok = rec.x != kDeadEdge;
         }
         if (!ok)
             continue;
@@ -991,7 +1010,7 @@ template <int kFT>
 __global__ void __launch_bounds__(kFT, 1024 / kFT)
 k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_t *out,
         int64_t *out_count, uint32_t n, uint32_t m, uint32_t wt, uint32_t vec, int32_t *csrc,
-        int32_t *cdst, uint32_t *cw)
+        int32_t *cdst, uint32_t *cw, uint32_t covered)
 {
     constexpr int kFW = kFT / 32;
     __shared__ TileSmem sm;
@@ -1026,7 +1045,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         dst = cdst;
         w = cw;
     }
-    uint32_t n_cur = n, m_cur = m, r = 0;
+    // m_cur: slots of the current list; m_live: its live edges (equal, except
+    // in the "covered" ablation, where the list keeps all m slots)
+    uint32_t n_cur = n, m_cur = m, m_live = m, r = 0;
     for (;; r++) {
         // hook + new ids of the roots
         const uint32_t nth = (n_cur + kHookWTile - 1) / kHookWTile;
@@ -1074,9 +1095,11 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             const uint32_t ntp = (m_cur + kCompWTile - 1) / kCompWTile;
             for (uint32_t t = gw; t < ntp; t += nw) {
                 if (r == 0)
-                    compact_pairs_wtile<true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
+                    compact_pairs_wtile<true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
+                                              covered != 0);
                 else
-                    compact_pairs_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
+                    compact_pairs_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
+                                               covered != 0);
             }
             mark_work(c);
             grid_sync(ws.bar, gen, status);
@@ -1104,10 +1127,18 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         // compact (+ find-min of the next round)
         const uint32_t ntc = (m_cur + kCompWTile - 1) / kCompWTile;
         for (uint32_t t = gw; t < ntc; t += nw) {
-            if (r == 0)
+            if (covered) {
+                if (r == 0)
+                    compact_wtile<true, true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
+                                              m_live);
+                else
+                    compact_wtile<false, true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
+                                               m_live);
+            } else if (r == 0) {
                 compact_wtile<true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
-            else
+            } else {
                 compact_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
+            }
         }
         mark_work(c);
         grid_sync(ws.bar, gen, status);
@@ -1118,8 +1149,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             c->stat_n[r + 1] = n_next;
         }
         n_cur = n_next;
-        m_cur = m_next;
-        if (m_cur == 0)
+        m_live = m_next;
+        m_cur = covered ? m : m_next;
+        if (m_live == 0)
             break;
         if (r + 1 >= (uint32_t)kMaxRounds || (ld_volatile_u32(status) & ST_TIMEOUT)) {
             if (gtid == 0)
@@ -1571,7 +1603,8 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
     // the fused kernel runs on any grid up to the co-resident one
     int g = grid > 0 && grid < s.grid_fused ? grid : s.grid_fused;
     int threads = s.fused_threads;
-    if (s.schedule == 0) {  // shape per solve: one CTA per SM, wider for large graphs
+    const uint32_t covered = s.schedule == 3 ? 1u : 0u;
+    if (s.schedule == 0 || s.schedule == 3) {  // shape per solve: one CTA per SM, wider for large graphs
         threads = m > kAutoWideM ? 1024 : 256;
         g = s.sms;
     }
@@ -1583,7 +1616,7 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
         uint32_t *cw = copy ? (uint32_t *)copy->w : nullptr;
         void *args[] = {(void *)&s.ws, (void *)&src, (void *)&dst, (void *)&wp, (void *)&out,
                         (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec,
-                        (void *)&csrc, (void *)&cdst, (void *)&cw};
+                        (void *)&csrc, (void *)&cdst, (void *)&cw, (void *)&covered};
         return cudaLaunchCooperativeKernel(fused_kernel(threads), dim3(g), dim3(threads), args,
                                            0, stream);
     }

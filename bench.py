@@ -8,7 +8,7 @@ emit) with the inputs already resident in HBM.  The 25 MB input fits in the
 the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config 1|2|3] [--no-cpu-baseline] [--schedule fused|graph|covered]
+                  [--config 1|2|3] [--no-cpu-baseline] [--schedule fused|graph|covered|cas]
   python bench.py --workload batched [--graphs G]     # C4: G graphs in one launch
   python bench.py --workload serving [--pool P] [--rates 1000,5000] [--seconds S]
   python bench.py --workload paper-cpu   (the paper's sequential comparison, host only)
@@ -297,8 +297,9 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     h = B.mst_create(dev, 0)
-    fused = args.schedule in ("fused", "covered")
-    B.mst_set_single_schedule(h, {"fused": 0, "graph": 2, "covered": 3}[args.schedule], 0, 0)
+    fused = args.schedule != "graph"
+    B.mst_set_single_schedule(h, {"fused": 0, "graph": 2, "covered": 3, "cas": 4}[args.schedule],
+                              0, 0)
 
     def solve():
         st = B.mst_solve(h, g.n, g.m, src, dst, w, out, cnt, stream)
@@ -741,8 +742,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     # covered: the ablation that flags internal edges in place instead of
-    # compacting the list (the sequential optimisation of Section 2.1)
-    ap.add_argument("--schedule", choices=["fused", "graph", "covered"], default="fused")
+    # compacting the list (the sequential optimisation of Section 2.1); cas:
+    # the ablation that hooks roots by compare-and-swap (Section 2.2.2)
+    ap.add_argument("--schedule", choices=["fused", "graph", "covered", "cas"], default="fused")
     ap.add_argument("--workload", choices=["single", "batched", "serving", "paper-cpu"],
                     default="single")
     ap.add_argument("--graphs", type=int, default=4096)

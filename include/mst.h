@@ -197,8 +197,12 @@ mst_status mst_profile_last_solve(mst_handle h, void *stream, mst_kernel_profile
  * round loop is a device-side conditional WHILE node; 3 = an ablation of
  * schedule 0 after the sequential "covered" optimisation (Section 2.1): the
  * edge list is never compacted, every round reads all m slots and edges that
- * became internal are flagged in their slot and skipped.  Results are
- * identical under every setting.
+ * became internal are flagged in their slot and skipped; 4 = an ablation of
+ * schedule 0 after the compare-and-swap algorithm (Section 2.2.2): each
+ * component's minimum edge joins the current roots of its endpoints by a
+ * compare-and-swap of the higher root's parent to the lower root, retried
+ * after fresh finds when it fails, and the roots left are numbered in a
+ * phase of their own.  Results are identical under every setting.
  */
 mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm,
                                    int block_threads);

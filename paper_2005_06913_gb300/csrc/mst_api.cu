@@ -432,7 +432,7 @@ mst_status mst_set_batched_schedule(mst_handle h, int schedule, int block_thread
 mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm,
                                    int block_threads)
 {
-    if (!h || schedule < 0 || schedule > 3 || blocks_per_sm < 0 || blocks_per_sm > 8 ||
+    if (!h || schedule < 0 || schedule > 4 || blocks_per_sm < 0 || blocks_per_sm > 8 ||
         (block_threads != 0 && block_threads != 256 && block_threads != 512 &&
          block_threads != 768 && block_threads != 1024))
         return MST_ERR_INVALID_ARG;

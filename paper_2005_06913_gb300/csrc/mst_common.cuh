@@ -35,7 +35,7 @@ constexpr uint32_t kTailLocalN = 1024;        // a one-CTA tail keeps arrays in 
 
 // Phase kinds of the fused solve's phase log.
 enum : uint8_t { PH_START = 0, PH_INIT, PH_FIND0, PH_HOOK, PH_COMPRESS, PH_COMPACT, PH_EMIT,
-                 PH_TAIL };
+                 PH_TAIL, PH_ROOTS };
 
 __device__ __forceinline__ unsigned long long global_timer_ns()
 {

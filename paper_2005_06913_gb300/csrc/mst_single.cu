@@ -44,6 +44,9 @@
 namespace mst {
 
 constexpr int kEmitWords = 128;  // bit words per emit tile: <= 4096 ids, fits the stage
+// Ablations of the fused solve (single-graph schedules 3 and 4)
+constexpr uint32_t kVariantCovered = 1u;  // flag internal edges in place, no compaction
+constexpr uint32_t kVariantCas = 2u;      // hook roots by compare-and-swap
 
 struct TileSmem {
     uint4 stage[kTile];  // ids of an emit tile / per-component arrays of a one-CTA tail
@@ -224,6 +227,118 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
                 red_or_u32(&ws.mst_bits[id[j] >> 5], 1u << (id[j] & 31));
             }
         }
+        mask[j] = __ballot_sync(0xffffffffu, root);
+        total += __popc(mask[j]);
+    }
+    uint32_t ex = 0;
+    if (lane == 0 && total)
+        ex = atomicAdd(&c->cnt_n[round], total);
+    ex = __shfl_sync(0xffffffffu, ex, 0);
+    const uint32_t lt = lanemask_lt();
+    uint32_t run = ex;
+#pragma unroll
+    for (int j = 0; j < kHookIpl; j++) {
+        if ((mask[j] >> lane) & 1u)
+            ws.nid[base + j * 32 + lane] = (int32_t)(run + __popc(mask[j] & lt));
+        run += __popc(mask[j]);
+    }
+}
+
+// The CAS-hook ablation (Section 2.2.2 on the GPU): each component with a
+// minimum edge joins the current trees of the edge's endpoints by one
+// compare-and-swap of a root's parent, while other threads do the same.
+// The higher-numbered root is hooked under the lower one, not the edge's
+// destination under its source: a root found first may be hooked before
+// the swap, and with a fixed edge direction that stale root can already
+// hang below the other one (a cycle); pointers that only ever go to lower
+// ids cannot close one.  Keys are totally ordered, so the minima of a round
+// are edges of the one minimum spanning forest: a failed swap only means
+// the root was hooked meanwhile (the finds are retried), and endpoints
+// found in one tree mean the edge was already added by the other component
+// it leaves.  Whether a component stays a root is known only after every
+// swap, so the roots are numbered in a phase of their own.
+constexpr uint32_t kCasRetryLimit = 1u << 16;
+constexpr uint32_t kNoRoot = 0xffffffffu;
+
+// Root of x while other threads hook roots: path halving.  Only a root's
+// pointer is swapped, and a non-root's pointer only moves to an ancestor, so
+// every pointer read stays an ancestor, ids fall along a path and a path has
+// fewer than n_cur hops (more would mean a broken forest: the status is set
+// and the find gives up).  Reads bypass L1: pointers change during the phase.
+__device__ __forceinline__ uint32_t cas_find(int32_t *parent, uint32_t x, uint32_t n_cur,
+                                             uint32_t *status)
+{
+    for (uint32_t s = 0; s <= n_cur; s++) {
+        const uint32_t p = (uint32_t)__ldcg(parent + x);
+        if (p == x)
+            return x;
+        const uint32_t gp = (uint32_t)__ldcg(parent + p);
+        if (gp != p)
+            __stcg(parent + x, (int32_t)gp);
+        x = gp;
+    }
+    atomicOr(status, ST_INTERNAL);
+    return kNoRoot;
+}
+
+template <bool R0>
+__device__ __forceinline__ void hook_cas_wtile(const Ws &ws, Ctl *c, uint32_t tile,
+                                               uint32_t round, uint32_t n_cur,
+                                               const int32_t *src, const int32_t *dst)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long *mcur = (round & 1) ? ws.mins[1] : ws.mins[0];
+    unsigned long long *mnext = (round & 1) ? ws.mins[0] : ws.mins[1];
+    int32_t *parent = ws.parent;
+    uint32_t *status = &c->status;
+    const uint32_t base = tile * kHookWTile;
+#pragma unroll 1
+    for (int j = 0; j < kHookIpl; j++) {
+        const uint32_t v = base + j * 32 + lane;
+        if (v >= n_cur)
+            continue;
+        const unsigned long long k = mcur[v];
+        mnext[v] = kNoEdge;
+        if (k == kNoEdge)
+            continue;
+        const uint32_t p = (uint32_t)k;
+        uint32_t a, b;
+        if (R0) {
+            a = (uint32_t)__ldg(src + p);
+            b = (uint32_t)__ldg(dst + p);
+        } else {
+            const uint2 e = __ldcg(ws.eends + p);
+            a = e.x;
+            b = e.y;
+        }
+        bool joined = false;
+        for (uint32_t t = 0; t < kCasRetryLimit && !joined; t++) {
+            const uint32_t c1 = cas_find(parent, a, n_cur, status);
+            const uint32_t c2 = cas_find(parent, b, n_cur, status);
+            const uint32_t lo = c1 < c2 ? c1 : c2, hi = c1 < c2 ? c2 : c1;
+            if (c1 == kNoRoot || c2 == kNoRoot || c1 == c2)
+                joined = true;  // (or given up, with the status set)
+            else if ((uint32_t)atomicCAS(parent + hi, (int32_t)hi, (int32_t)lo) == hi) {
+                red_or_u32(&ws.mst_bits[p >> 5], 1u << (p & 31));
+                joined = true;
+            }
+        }
+        if (!joined)
+            atomicOr(status, ST_INTERNAL);
+    }
+}
+
+// New ids of the roots left after the CAS hooks (one warp tile).
+__device__ __forceinline__ void number_roots_wtile(const Ws &ws, Ctl *c, uint32_t tile,
+                                                   uint32_t round, uint32_t n_cur)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t base = tile * kHookWTile;
+    uint32_t mask[kHookIpl], total = 0;
+#pragma unroll
+    for (int j = 0; j < kHookIpl; j++) {
+        const uint32_t v = base + j * 32 + lane;
+        const bool root = v < n_cur && (uint32_t)__ldcg(ws.parent + v) == v;
         mask[j] = __ballot_sync(0xffffffffu, root);
         total += __popc(mask[j]);
     }
@@ -1010,8 +1125,9 @@ template <int kFT>
 __global__ void __launch_bounds__(kFT, 1024 / kFT)
 k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_t *out,
         int64_t *out_count, uint32_t n, uint32_t m, uint32_t wt, uint32_t vec, int32_t *csrc,
-        int32_t *cdst, uint32_t *cw, uint32_t covered)
+        int32_t *cdst, uint32_t *cw, uint32_t variant)
 {
+    const bool covered = (variant & kVariantCovered) != 0, cas = (variant & kVariantCas) != 0;
     constexpr int kFW = kFT / 32;
     __shared__ TileSmem sm;
     Ctl *c = ws.ctl;
@@ -1022,6 +1138,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
     uint32_t gen = 0;  // barrier count (the barrier itself keeps no generation)
     log_phase(c, PH_START);
     init_range(ws, n, m, gtid, gstride);
+    if (cas)  // the CAS hook swaps roots' pointers: every component starts as one
+        for (size_t v = gtid; v < n; v += gstride)
+            ws.parent[v] = (int32_t)v;
     mark_work(c);
     if (gtid == 0) {
         c->n = n;
@@ -1054,14 +1173,27 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         if (bid == 0 && threadIdx.x == 0)
             c->flag3[0] = 0;
         for (uint32_t t = gw; t < nth; t += nw) {
-            if (r == 0)
+            if (cas) {
+                if (r == 0)
+                    hook_cas_wtile<true>(ws, c, t, r, n_cur, src, dst);
+                else
+                    hook_cas_wtile<false>(ws, c, t, r, n_cur, src, dst);
+            } else if (r == 0) {
                 hook_wtile<true>(ws, c, t, r, n_cur, src, dst);
-            else
+            } else {
                 hook_wtile<false>(ws, c, t, r, n_cur, src, dst);
+            }
         }
         mark_work(c);
         grid_sync(ws.bar, gen, status);
         log_phase(c, PH_HOOK, r);
+        if (cas) {
+            for (uint32_t t = gw; t < nth; t += nw)
+                number_roots_wtile(ws, c, t, r, n_cur);
+            mark_work(c);
+            grid_sync(ws.bar, gen, status);
+            log_phase(c, PH_ROOTS, r);
+        }
         const uint32_t n_next = ld_volatile_u32(&c->cnt_n[r]);
         // few components left: this round's compaction feeds the tail instead
         const bool tail = n_next >= 2 && n_next <= kTailMaxN && m_cur > 0;
@@ -1096,10 +1228,10 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             for (uint32_t t = gw; t < ntp; t += nw) {
                 if (r == 0)
                     compact_pairs_wtile<true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
-                                              covered != 0);
+                                              covered);
                 else
                     compact_pairs_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
-                                               covered != 0);
+                                               covered);
             }
             mark_work(c);
             grid_sync(ws.bar, gen, status);
@@ -1125,6 +1257,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             break;
         }
         // compact (+ find-min of the next round)
+        if (cas)  // the next round's components start as roots
+            for (size_t v = gtid; v < n_next; v += gstride)
+                ws.parent[v] = (int32_t)v;
         const uint32_t ntc = (m_cur + kCompWTile - 1) / kCompWTile;
         for (uint32_t t = gw; t < ntc; t += nw) {
             if (covered) {
@@ -1603,8 +1738,9 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
     // the fused kernel runs on any grid up to the co-resident one
     int g = grid > 0 && grid < s.grid_fused ? grid : s.grid_fused;
     int threads = s.fused_threads;
-    const uint32_t covered = s.schedule == 3 ? 1u : 0u;
-    if (s.schedule == 0 || s.schedule == 3) {  // shape per solve: one CTA per SM, wider for large graphs
+    const uint32_t variant =
+        s.schedule == 3 ? kVariantCovered : s.schedule == 4 ? kVariantCas : 0u;
+    if (s.schedule == 0 || s.schedule >= 3) {  // shape per solve: one CTA per SM, wider for large graphs
         threads = m > kAutoWideM ? 1024 : 256;
         g = s.sms;
     }
@@ -1616,7 +1752,7 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
         uint32_t *cw = copy ? (uint32_t *)copy->w : nullptr;
         void *args[] = {(void *)&s.ws, (void *)&src, (void *)&dst, (void *)&wp, (void *)&out,
                         (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec,
-                        (void *)&csrc, (void *)&cdst, (void *)&cw, (void *)&covered};
+                        (void *)&csrc, (void *)&cdst, (void *)&cw, (void *)&variant};
         return cudaLaunchCooperativeKernel(fused_kernel(threads), dim3(g), dim3(threads), args,
                                            0, stream);
     }
@@ -1740,7 +1876,7 @@ cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<Ker
     Ctl c;
     MST_TRY(cudaMemcpy(&c, s.ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
     static const char *names[] = {"start", "init", "find0", "hook",
-                                  "compress", "compact", "emit", "tail"};
+                                  "compress", "compact", "emit", "tail", "roots"};
     const double n = c.n, m = c.m;
     auto bytes_of = [&](int kind, uint32_t r) -> double {
         switch (kind) {
@@ -1768,7 +1904,7 @@ cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<Ker
     double wait_ms = 0.0;
     int waits = 0;
     for (uint32_t i = 1; i < np; i++) {
-        const int k = c.phase_kind[i] < 8 ? c.phase_kind[i] : 0;
+        const int k = c.phase_kind[i] <= PH_ROOTS ? c.phase_kind[i] : 0;
         const uint32_t r = c.phase_round[i];
         const double ms = (double)(c.phase_ns[i] - c.phase_ns[i - 1]) * 1e-6;
         double b = bytes_of(k, r < (uint32_t)kMaxRounds ? r : 0);
@@ -1777,7 +1913,7 @@ cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<Ker
             last_compress_round = r;
         }
         std::string name = std::string("k_solve:") + names[k];
-        if (k == PH_HOOK || k == PH_COMPRESS || k == PH_COMPACT)
+        if (k == PH_HOOK || k == PH_COMPRESS || k == PH_COMPACT || k == PH_ROOTS)
             name += r == 0 ? "@r0" : "@r1+";
         add(name, ms, b);
         if (c.work_ns[i] > c.phase_ns[i - 1] && c.work_ns[i] <= c.phase_ns[i]) {

@@ -41,7 +41,8 @@ def check(h, n, src, dst, w):
     return got
 
 
-@pytest.fixture(params=[0, 1, 2, 3], ids=["fused-auto", "fused-fixed", "graph", "covered"])
+@pytest.fixture(params=[0, 1, 2, 3, 4],
+                ids=["fused-auto", "fused-fixed", "graph", "covered", "cas-hook"])
 def sched(request, handle):
     """Runs a test under each single-graph schedule."""
     assert B.mst_set_single_schedule(handle, request.param, 0) == B.MST_OK
@@ -70,7 +71,7 @@ def test_fused_grid_sizes(handle, bps, threads):
 
 
 def test_schedule_arg_errors(handle):
-    for bad in [(4, 0, 0), (-1, 0, 0), (1, 9, 0), (1, -1, 0), (1, 0, 100), (1, 0, 2048)]:
+    for bad in [(5, 0, 0), (-1, 0, 0), (1, 9, 0), (1, -1, 0), (1, 0, 100), (1, 0, 2048)]:
         assert B.mst_set_single_schedule(handle, *bad) == B.MST_ERR_INVALID_ARG
 
 

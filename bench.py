@@ -194,6 +194,26 @@ def cpu_baseline(g, budget_s: float = 12.0):
                       f"(m={g.m}), {reps} solves in {dt:.1f} s"}
 
 
+def cpu_parallel_baseline(g, budget_s: float = 5.0):
+    """The paper's own parallel algorithm (Section 2.2.2, compare-and-swap
+    joins, every thread sweeping all edges) on every host core, repeated
+    until about budget_s seconds; Medges/s.  Context for the GPU number."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    reps, rounds, threads = 0, 0, 0
+    while True:
+        _, rounds, threads = oracle.boruvka_cas_parallel(g.n, g.src, g.dst, g.w, 0)
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": g.m * reps / dt / 1e6, "unit": UNIT, "cores": threads,
+            "kind": "paper parallel Boruvka (Section 2.2.2, CAS joins, pthreads)",
+            "sample": f"oracle/mst_cpu_parallel.c on the full workload (m={g.m}), "
+                      f"{reps} solves in {dt:.1f} s, {rounds} rounds"}
+
+
 REFERENCE_BUDGET_S = 150.0  # whole timed run of the reference arm
 
 
@@ -407,6 +427,7 @@ def run_ours(args):
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g)
+        line["cpu_parallel_baseline"] = cpu_parallel_baseline(g)
     B.mst_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -696,15 +717,18 @@ PAPER_TABLE1 = ["Graph10K_3", "Graph10K_6", "Graph10K_9", "Graph100K_3", "Graph1
 
 
 def run_paper_cpu(args):
-    """The paper's sequential comparison (Section 2.1 "Optimization", Fig. 1:
-    the covered-edge optimisation makes sequential Boruvka 24-45% faster) on
-    the Table 1 shapes, with the oracle on this host's cores, one thread:
-    sequential Boruvka without and with the optimisation, and Kruskal; the
-    median of 3 runs each.  No GPU work."""
+    """The paper's CPU comparisons on the Table 1 shapes, on this host: the
+    sequential one (Section 2.1 "Optimization", Fig. 1: the covered-edge
+    optimisation makes sequential Boruvka 24-45% faster), sequential Boruvka
+    without and with the optimisation and Kruskal on one thread; and the
+    parallel one (Section 4, Figs. 3-4), the compare-and-swap algorithm on 1
+    to all host threads.  The median of 3 runs each.  No GPU work."""
     import oracle
     from paper_2005_06913_gb300 import graphgen as gg
 
     oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = sorted({t for t in (1, 2, 4, 8, 16, cores) if t <= cores})
     rows = []
     for name in PAPER_TABLE1:
         g = gg.paper_table1(name)
@@ -721,10 +745,23 @@ def run_paper_cpu(args):
             row[label + "_ms"] = round(statistics.median(ts) * 1e3, 2)
         plain, cov = row["boruvka_plain_ms"], row["boruvka_covered_ms"]
         row["covered_time_saved_pct"] = round(100.0 * (plain - cov) / plain, 1)
+        # the paper's parallel algorithm (Section 2.2.2, Figs. 3-4) by threads
+        par = {}
+        for t in threads:
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                oracle.boruvka_cas_parallel(g.n, g.src, g.dst, g.w, t)
+                ts.append(time.perf_counter() - t0)
+            par[str(t)] = round(statistics.median(ts) * 1e3, 2)
+        row["cas_parallel_ms_by_threads"] = par
+        row["cas_speedup_best_vs_plain"] = round(plain / min(par.values()), 2)
+        row["cas_speedup_best_vs_covered"] = round(cov / min(par.values()), 2)
         rows.append(row)
     print(json.dumps({"metric": "sequential Boruvka time without and with the covered-edge "
-                                "optimisation, and Kruskal (oracle, one host thread)",
-                      "impl": "oracle", "unit": "ms", "cores": 1, "data": "synthetic",
+                                "optimisation, and Kruskal (oracle, one host thread); the "
+                                "paper's parallel CAS Boruvka by host threads",
+                      "impl": "oracle", "unit": "ms", "cores": cores, "data": "synthetic",
                       "config": {"workload": "the paper's Table 1 shapes (random connected, "
                                              "n in 10K/100K/1M, degree 3/6/9)"},
                       "rows": rows}), flush=True)

@@ -105,6 +105,39 @@ mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
                         const int32_t *src, const int32_t *dst, const void *w,
                         int32_t *out_edge_ids, int64_t *out_count, void *stream);
 
+/* Flags of mst_solve_csr. */
+#define MST_CSR_SYMMETRIC 1u
+
+/*
+ * Minimum spanning forest of a graph given as an adjacency CSR (a layout
+ * the paper does not use: its graphs are edge lists, Section 2.1 data
+ * structures).  row_ptr (device, int64, n+1 entries) holds the offsets of
+ * each vertex's entries; col (device, int32, nnz) the other endpoint and w
+ * (device, uint32 or float32 per wt, nnz) the weight of each entry.  Entry
+ * p of row u is the edge (u, col[p]) with id p, so out_edge_ids (device,
+ * capacity >= max(n-1,0)) receives CSR positions, ascending, and
+ * *out_count (device int64) their number: the same result as mst_solve_ex
+ * on the edge list (row of p, col[p], w[p]).  With MST_CSR_SYMMETRIC the
+ * caller declares every undirected edge stored from both ends with one
+ * weight; the copy in the higher row can then never enter the tree (the
+ * lower position wins the tie) and is skipped, which halves the edges of
+ * the later rounds without changing the result.  Entries in the higher row
+ * without a mirror are dropped under that flag.
+ * The row of each entry is written into device memory owned by the handle
+ * (4 B per entry, grown on demand, counted in the memory budget), so
+ * row_ptr, col and w are not modified and need not outlive the call's
+ * stream work.  With nnz = 0, row_ptr is not read.  A malformed offset
+ * table (row_ptr[0] != 0, row_ptr[n] != nnz, or decreasing offsets) is
+ * reported on the device as MST_ERR_INVALID_ARG by mst_get_status, as a bad
+ * vertex id in col is.  Host errors: MST_ERR_INVALID_ARG for a NULL handle,
+ * bad wt or flags, negative sizes, nnz > INT32_MAX or missing pointers;
+ * MST_ERR_BUDGET or MST_ERR_OOM when the row buffer cannot grow.
+ */
+mst_status mst_solve_csr(mst_handle h, mst_weight_type wt, int32_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col, const void *w,
+                         uint32_t flags, int32_t *out_edge_ids, int64_t *out_count,
+                         void *stream);
+
 /*
  * Host-buffer form of mst_solve_ex for callers whose graph is in host memory
  * (src, dst, w are host pointers).  If all three are page-locked (pinned)

@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mst_oracle.c")
+_SRC_MT = os.path.join(_HERE, "mst_cpu_parallel.c")
 _LIB = os.path.join(_HERE, "libmst_oracle.so")
 _lib = None
 
@@ -28,15 +29,16 @@ _P = ctypes.c_void_p
 
 
 def build(force: bool = False) -> str:
-    """Compile ``mst_oracle.c`` into ``libmst_oracle.so`` (gcc, -O2)."""
+    """Compile ``mst_oracle.c`` and ``mst_cpu_parallel.c`` into
+    ``libmst_oracle.so`` (gcc, -O2, POSIX threads)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_MT))):
         return _LIB
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
     try:
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC",
-                               "-Wall", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread",
+                               "-Wall", "-o", tmp, _SRC, _SRC_MT])
         os.replace(tmp, _LIB)
     finally:
         if os.path.exists(tmp):
@@ -53,6 +55,8 @@ def _bind(path):
         f.argtypes = [_I64, _I64, _P, _P, _P, ctypes.c_int, _P]
     lib.orc_boruvka.restype = _I64
     lib.orc_boruvka.argtypes = [_I64, _I64, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P]
+    lib.orc_boruvka_cas_mt.restype = _I64
+    lib.orc_boruvka_cas_mt.argtypes = [_I64, _I64, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P]
     lib.orc_components.restype = _I64
     lib.orc_components.argtypes = [_I64, _I64, _P, _P]
     for name in ("orc_check_cycle_property", "orc_check_cut_property"):
@@ -116,6 +120,25 @@ def boruvka(n, src, dst, w, covered: bool = True):
                              w.ctypes.data, wt, int(bool(covered)), flags.ctypes.data,
                              ctypes.addressof(rounds))
     return _ids(rc, flags[:src.shape[0]]), int(rounds.value)
+
+
+def boruvka_cas_parallel(n, src, dst, w, threads: int = 0):
+    """The Section 2.2.2 parallel Boruvka (compare-and-swap joins) on
+    ``threads`` host threads (0 = every core).  A CPU baseline, checked
+    against Kruskal by the tests.  Returns ``(ids, rounds, threads)``."""
+    n, src, dst, w, wt = _prep(n, src, dst, w)
+    if threads <= 0:
+        threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") \
+            else (os.cpu_count() or 1)
+    threads = max(1, min(int(threads), 256))
+    flags = np.zeros(max(src.shape[0], 1), np.uint8)
+    rounds = ctypes.c_int64(0)
+    rc = _load().orc_boruvka_cas_mt(n, src.shape[0], src.ctypes.data, dst.ctypes.data,
+                                    w.ctypes.data, wt, threads, flags.ctypes.data,
+                                    ctypes.addressof(rounds))
+    if rc == -3:
+        raise RuntimeError("could not start the worker threads")
+    return _ids(rc, flags[:src.shape[0]]), int(rounds.value), threads
 
 
 def prim(n, src, dst, w) -> np.ndarray:

@@ -43,6 +43,7 @@ _SIGS = {
     "mst_solve": (_INT, [_P, _I32, _I64, _P, _P, _P, _P, _P, _P]),
     "mst_solve_ex": (_INT, [_P, _INT, _I32, _I64, _P, _P, _P, _P, _P, _P]),
     "mst_solve_host": (_INT, [_P, _INT, _I32, _I64, _P, _P, _P, _P, _P, _P]),
+    "mst_solve_csr": (_INT, [_P, _INT, _I32, _I64, _P, _P, _P, ctypes.c_uint32, _P, _P, _P]),
     "mst_profile_last_solve": (_INT, [_P, _P, _P, _I32, ctypes.POINTER(_I32)]),
     "mst_solve_batched": (_INT, [_P, _INT, _I32, _P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P]),
     "mst_get_status": (_INT, [_P, _P]),
@@ -133,6 +134,17 @@ def mst_solve(h, n, m, src, dst, w, out_edge_ids, out_count, stream=None) -> int
 def mst_solve_ex(h, wt, n, m, src, dst, w, out_edge_ids, out_count, stream=None) -> int:
     return lib().mst_solve_ex(h, int(wt), int(n), int(m), _ptr(src), _ptr(dst), _ptr(w),
                               _ptr(out_edge_ids), _ptr(out_count), _stream(stream))
+
+
+MST_CSR_SYMMETRIC = 1
+
+
+def mst_solve_csr(h, wt, n, nnz, row_ptr, col, w, flags, out_edge_ids, out_count,
+                  stream=None) -> int:
+    """Adjacency-CSR solve: row_ptr (int64, n+1), col (int32), w on the
+    device; the tree's ids are CSR positions."""
+    return lib().mst_solve_csr(h, int(wt), int(n), int(nnz), _ptr(row_ptr), _ptr(col), _ptr(w),
+                               int(flags), _ptr(out_edge_ids), _ptr(out_count), _stream(stream))
 
 
 def mst_solve_host(h, wt, n, m, src, dst, w, out_edge_ids, out_count, stream=None) -> int:

@@ -92,6 +92,8 @@ mst_status mst_destroy(mst_handle h)
     batched_release(h->batched);
     if (h->staging)
         cudaFree(h->staging);
+    if (h->csr_rows)
+        cudaFree(h->csr_rows);
     for (cudaStream_t cs : h->copy_stream)
         if (cs)
             cudaStreamDestroy(cs);
@@ -173,6 +175,45 @@ mst_status mst_solve_ex(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,
         return MST_ERR_CUDA;
     return solve_single(h, wt, n, m, src, dst, w, out_edge_ids, out_count, (cudaStream_t)stream,
                         nullptr);
+}
+
+mst_status mst_solve_csr(mst_handle h, mst_weight_type wt, int32_t n, int64_t nnz,
+                         const int64_t *row_ptr, const int32_t *col, const void *w,
+                         uint32_t flags, int32_t *out_edge_ids, int64_t *out_count, void *stream)
+{
+    if (!h || (wt != MST_W_U32 && wt != MST_W_F32) || (flags & ~(uint32_t)MST_CSR_SYMMETRIC))
+        return MST_ERR_INVALID_ARG;
+    mst_status st = check_graph_args(n, nnz, col, col, w, out_edge_ids, out_count);
+    if (st != MST_OK)
+        return st;
+    if (nnz > 0 && !row_ptr)
+        return MST_ERR_INVALID_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess)
+        return MST_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((size_t)nnz > h->csr_cap) {
+        const size_t bytes = (size_t)nnz * sizeof(int32_t);
+        if (h->budget && bytes + h->staging_bytes + h->single.bytes + h->batched.bytes > h->budget)
+            return MST_ERR_BUDGET;
+        cudaStreamSynchronize(s);  // the old buffer may be in use by earlier work
+        if (h->csr_rows)
+            cudaFree(h->csr_rows);
+        h->csr_rows = nullptr;
+        h->csr_cap = 0;
+        if (cudaMalloc(&h->csr_rows, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return MST_ERR_OOM;
+        }
+        h->csr_cap = (size_t)nnz;
+    }
+    if (nnz > 0) {
+        cudaError_t e = csr_rows(row_ptr, col, (uint32_t)n, (uint32_t)nnz,
+                                 (flags & MST_CSR_SYMMETRIC) != 0, h->csr_rows, h->num_sms, s);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+    }
+    return solve_single(h, wt, n, nnz, nnz > 0 ? h->csr_rows : nullptr, col, w, out_edge_ids,
+                        out_count, s, nullptr);
 }
 
 mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m,

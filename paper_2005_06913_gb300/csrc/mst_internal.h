@@ -63,6 +63,10 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n,
                           uint32_t m, cudaStream_t stream, int grid = 0, const InputCopy *copy = nullptr);
 double single_alg_bytes(const Ctl &c);
+// Row of every entry of an adjacency CSR (mst_csr.cu); a malformed offset
+// table marks entry 0 with row -1.
+cudaError_t csr_rows(const int64_t *row_ptr, const int32_t *col, uint32_t n, uint32_t nnz,
+                     bool symmetric, int32_t *rows, int num_sms, cudaStream_t stream);
 // Per-phase times of the last fused solve (its own phase log; synchronous).
 cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<KernelProfile> &prof);
 // Replays a solve kernel by kernel between CUDA events (synchronous).
@@ -164,6 +168,8 @@ struct mst_handle_s {
     LastSolve last_solve;
     void *staging = nullptr;  // device staging of mst_solve_host
     size_t staging_bytes = 0;
+    int32_t *csr_rows = nullptr;  // row of each CSR entry (mst_solve_csr)
+    size_t csr_cap = 0;           // entries
     cudaStream_t copy_stream[2] = {nullptr, nullptr};  // its input copies run side by side
     cudaEvent_t copy_event[3] = {nullptr, nullptr, nullptr};
     size_t budget = 0;  // 0 = unlimited

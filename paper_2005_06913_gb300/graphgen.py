@@ -13,7 +13,9 @@ generators stand in for them with five workload families of the same shape:
 * ``batched``           many ``random_connected`` graphs of log-uniform size,
   concatenated with int64 offset tables;
 * ``serving_pool``      a pool of ``random_connected`` graphs with float32
-  weights, replayed by the serving benchmark.
+  weights, replayed by the serving benchmark;
+* ``to_csr``            any of these as an adjacency CSR (each undirected
+  edge stored from both ends), and ``csr_entries`` back to per-entry COO.
 
 Every generator is a pure function of its arguments and seed (numpy PCG64).
 Nothing here computes a spanning tree or any part of one: the module only
@@ -30,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "Graph", "Batch", "random_connected", "grid2d", "rmat", "batched",
-    "serving_pool", "paper_table1", "permutation_weights",
+    "serving_pool", "paper_table1", "permutation_weights", "CSR", "to_csr", "csr_entries",
 ]
 
 SEED_BASE = 0x4D5354  # "MST"
@@ -278,6 +280,47 @@ def batched(G: int, nmin: int, nmax: int, degree: int, seed: int,
                  cat([p.dst for p in parts], np.int32), cat([p.w for p in parts], wdt),
                  f"batched(G={G},n=[{nmin},{nmax}],deg={degree})",
                  [int(s) for s in subseeds])
+
+
+@dataclass
+class CSR:
+    """An adjacency CSR: entry p of row u is the edge (u, col[p]) with id p."""
+
+    n: int
+    row_ptr: np.ndarray  # int64 [n+1]
+    col: np.ndarray      # int32 [nnz]
+    w: np.ndarray        # uint32 or float32 [nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+
+def to_csr(g: Graph, symmetric: bool = True) -> CSR:
+    """``g`` as an adjacency CSR.  With ``symmetric`` every edge is stored
+    from both ends with its weight (self-loops once); otherwise only from
+    its ``src``.  Rows are in vertex order and, within a row, entries keep
+    the order of the edge ids."""
+    if symmetric:
+        loop = g.src == g.dst
+        u = np.concatenate([g.src, g.dst[~loop]])
+        v = np.concatenate([g.dst, g.src[~loop]])
+        w = np.concatenate([g.w, g.w[~loop]])
+        eid = np.concatenate([np.arange(g.m), np.flatnonzero(~loop)])
+    else:
+        u, v, w, eid = g.src, g.dst, g.w, np.arange(g.m)
+    order = np.lexsort((eid, u))
+    counts = np.bincount(u, minlength=g.n).astype(np.int64)
+    row_ptr = np.zeros(g.n + 1, np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return CSR(g.n, row_ptr, np.ascontiguousarray(v[order], np.int32),
+               np.ascontiguousarray(w[order]))
+
+
+def csr_entries(c: CSR) -> Graph:
+    """The CSR's entries as an edge list: edge p = (row of p, col[p])."""
+    rows = np.repeat(np.arange(c.n, dtype=np.int32), np.diff(c.row_ptr))
+    return Graph(c.n, rows, c.col.copy(), c.w.copy(), "csr-entries")
 
 
 def serving_pool(P: int, nmin: int, nmax: int, degree: int, seed: int) -> Batch:

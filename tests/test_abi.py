@@ -40,6 +40,7 @@ def test_every_handle_entry_point_rejects_null(lib_built):
     done = ctypes.c_int(0)
     cnt = ctypes.c_int32(0)
     assert L.mst_solve_host(None, 0, 4, 3, None, None, None, None, None, None) == bad
+    assert L.mst_solve_csr(None, 0, 4, 6, None, None, None, 0, None, None, None) == bad
     assert L.mst_solve_batched(None, 0, 1, None, None, 4, 3, None, None, None, None, None,
                                None) == bad
     assert L.mst_autotune_batched(None, 0, 1, None, None, 4, 3, None, None, None, None, None,

@@ -38,8 +38,8 @@ def build_mutant(tmp_path, old, new):
     path = tmp_path / "mutant.c"
     path.write_text(text.replace(old, new, 1))
     so = tmp_path / "mutant.so"
-    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-shared", "-fPIC", "-w",
-                           "-o", str(so), str(path)])
+    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-w",
+                           "-o", str(so), str(path), oracle._SRC_MT])
     return oracle._bind(str(so))
 
 

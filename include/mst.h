@@ -69,8 +69,10 @@ const char *mst_status_string(mst_status s);
 
 /*
  * Creates a handle on CUDA device `device`.  mem_budget_bytes caps the
- * workspace this handle may allocate (0 = no cap); a solve whose workspace
- * would exceed it returns MST_ERR_BUDGET.  *h receives the handle.
+ * device memory this handle may allocate (0 = no cap): the single-graph and
+ * batched workspaces, the staging of mst_solve_host and the row buffer of
+ * mst_solve_csr, together; a solve whose growth would exceed it returns
+ * MST_ERR_BUDGET.  *h receives the handle.
  */
 mst_status mst_create(mst_handle *h, int device, size_t mem_budget_bytes);
 

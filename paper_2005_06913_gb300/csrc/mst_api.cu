@@ -104,6 +104,13 @@ mst_status mst_destroy(mst_handle h)
     return MST_OK;
 }
 
+// Bytes the handle holds outside the single and batched workspaces: the
+// host-buffer staging and the CSR row buffer (all counted in the budget).
+static size_t aux_bytes(const mst_handle h)
+{
+    return h->staging_bytes + h->csr_cap * sizeof(int32_t);
+}
+
 static mst_status check_graph_args(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                    const void *w, int32_t *out, int64_t *out_count)
 {
@@ -142,7 +149,7 @@ static mst_status solve_single(mst_handle h, mst_weight_type wt, int32_t n, int6
         uint32_t n_cap = nn > h->single.ws.n_cap ? nn : h->single.ws.n_cap;
         uint32_t m_cap = mm > h->single.ws.m_cap ? mm : h->single.ws.m_cap;
         if (h->budget && single_bytes(n_cap < 1024 ? 1024 : n_cap, m_cap < 1024 ? 1024 : m_cap) +
-                                 h->batched.bytes > h->budget)
+                                 h->batched.bytes + aux_bytes(h) > h->budget)
             return MST_ERR_BUDGET;
         cudaStreamSynchronize(s);  // workspace may be in use by earlier work
         cudaError_t e = single_reserve(h->single, h->device, nn, mm);
@@ -232,7 +239,8 @@ mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t need = 3 * al(eb) + al((size_t)(n > 1 ? n - 1 : 1) * 4) + al(8);
     if (need > h->staging_bytes) {
-        if (h->budget && need + h->single.bytes + h->batched.bytes > h->budget)
+        if (h->budget && need + h->csr_cap * sizeof(int32_t) + h->single.bytes +
+                                 h->batched.bytes > h->budget)
             return MST_ERR_BUDGET;
         cudaStreamSynchronize(s);
         if (h->staging)
@@ -444,8 +452,8 @@ mst_status mst_solve_batched(mst_handle h, mst_weight_type wt, int32_t G, const 
     h->last = LAST_BATCHED;
     if (G == 0)
         return MST_OK;
-    if (h->budget && batched_bytes(G, (uint64_t)total_n, (uint64_t)total_m) + h->single.bytes >
-                         h->budget)
+    if (h->budget && batched_bytes(G, (uint64_t)total_n, (uint64_t)total_m) + h->single.bytes +
+                             aux_bytes(h) > h->budget)
         return MST_ERR_BUDGET;
     cudaError_t e = batched_reserve(h->batched, G, (uint64_t)total_n, (uint64_t)total_m);
     if (e != cudaSuccess) {
@@ -510,8 +518,8 @@ mst_status mst_autotune_batched(mst_handle h, mst_weight_type wt, int32_t G,
         return MST_OK;
     if (cudaSetDevice(h->device) != cudaSuccess)
         return MST_ERR_CUDA;
-    if (h->budget && batched_bytes(G, (uint64_t)total_n, (uint64_t)total_m) + h->single.bytes >
-                         h->budget)
+    if (h->budget && batched_bytes(G, (uint64_t)total_n, (uint64_t)total_m) + h->single.bytes +
+                             aux_bytes(h) > h->budget)
         return MST_ERR_BUDGET;
     cudaError_t e = batched_reserve(h->batched, G, (uint64_t)total_n, (uint64_t)total_m);
     if (e != cudaSuccess) {

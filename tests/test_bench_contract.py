@@ -49,3 +49,14 @@ def test_traffic_table_lookup(tmp_path, monkeypatch):
                                         (list(range(1, 101)), 51, 99)])
 def test_percentiles(xs, p50, p99):
     assert bench._percentiles(xs) == (p50, p99)
+
+
+def test_cpu_baselines_on_a_small_graph():
+    from paper_2005_06913_gb300 import graphgen as gg
+    g = gg.random_connected(2000, 8000, 3)
+    seq = bench.cpu_baseline(g, budget_s=0.05)
+    par = bench.cpu_parallel_baseline(g, budget_s=0.05)
+    assert seq["kind"] == "oracle" and seq["cores"] == 1 and seq["value"] > 0
+    assert par["cores"] >= 1 and par["value"] > 0 and "2.2.2" in par["kind"]
+    assert par["unit"] == seq["unit"] == bench.UNIT
+

@@ -52,3 +52,15 @@ def test_bad_ids_rejected(oracle_mod):
     with pytest.raises(ValueError):
         oracle_mod.boruvka_cas_parallel(3, np.array([0], np.int32), np.array([3], np.int32),
                                         np.array([1], np.uint32), 2)
+
+
+def test_golden_fixtures(oracle_mod):
+    """The paper's own small examples (tests/golden), at several thread counts."""
+    import os
+    from test_oracle import GOLDEN, arrays, load_golden
+    for name in sorted(os.listdir(GOLDEN)):
+        n, edges, mst = load_golden(os.path.join(GOLDEN, name))
+        src, dst, w = arrays(edges)
+        for t in (1, 2, 3):
+            got, _, _ = oracle_mod.boruvka_cas_parallel(n, src, dst, w, t)
+            assert got.tolist() == sorted(mst), (name, t)

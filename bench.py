@@ -176,6 +176,31 @@ def dist_env():
     return ws, rank, local
 
 
+def host_info():
+    """The host the CPU baselines ran on: architecture, CPU model, cores."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"arch": platform.machine(), "model": model, "cores_available": cores}
+
+
 def cpu_baseline(g, budget_s: float = 12.0):
     """The oracle (Kruskal, one thread) on the full workload, repeated until
     about budget_s seconds of CPU work; Medges/s."""
@@ -191,7 +216,8 @@ def cpu_baseline(g, budget_s: float = 12.0):
     dt = time.perf_counter() - t0
     return {"value": g.m * reps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"oracle Kruskal (oracle/mst_oracle.c, 1 thread) on the full workload "
-                      f"(m={g.m}), {reps} solves in {dt:.1f} s"}
+                      f"(m={g.m}), {reps} solves in {dt:.1f} s",
+            "host": host_info()}
 
 
 def cpu_parallel_baseline(g, budget_s: float = 5.0):
@@ -211,7 +237,8 @@ def cpu_parallel_baseline(g, budget_s: float = 5.0):
     return {"value": g.m * reps / dt / 1e6, "unit": UNIT, "cores": threads,
             "kind": "paper parallel Boruvka (Section 2.2.2, CAS joins, pthreads)",
             "sample": f"oracle/mst_cpu_parallel.c on the full workload (m={g.m}), "
-                      f"{reps} solves in {dt:.1f} s, {rounds} rounds"}
+                      f"{reps} solves in {dt:.1f} s, {rounds} rounds",
+            "host": host_info()}
 
 
 REFERENCE_BUDGET_S = 150.0  # whole timed run of the reference arm
@@ -255,7 +282,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": wname, "n": g.n, "m": g.m},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -761,7 +788,8 @@ def run_paper_cpu(args):
     print(json.dumps({"metric": "sequential Boruvka time without and with the covered-edge "
                                 "optimisation, and Kruskal (oracle, one host thread); the "
                                 "paper's parallel CAS Boruvka by host threads",
-                      "impl": "oracle", "unit": "ms", "cores": cores, "data": "synthetic",
+                      "impl": "oracle", "unit": "ms", "cores": cores, "host": host_info(),
+                      "data": "synthetic",
                       "config": {"workload": "the paper's Table 1 shapes (random connected, "
                                              "n in 10K/100K/1M, degree 3/6/9)"},
                       "rows": rows}), flush=True)

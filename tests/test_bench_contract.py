@@ -59,4 +59,5 @@ def test_cpu_baselines_on_a_small_graph():
     assert seq["kind"] == "oracle" and seq["cores"] == 1 and seq["value"] > 0
     assert par["cores"] >= 1 and par["value"] > 0 and "2.2.2" in par["kind"]
     assert par["unit"] == seq["unit"] == bench.UNIT
+    assert seq["host"]["arch"] and seq["host"]["cores_available"] >= 1
 

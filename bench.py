@@ -87,6 +87,9 @@ def traffic_for(kernel: str, workload):
     return None
 
 
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (context beside the measured peak)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -413,6 +416,7 @@ def run_ours(args):
     achieved = dom_bytes / dom_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak,
+                "frac_of_nominal": achieved / HBM_NOMINAL_GBS,  # GB300's 7.9 TB/s
                 # counters were taken under the default schedule only
                 "traffic": traffic_for(dom_name, TRAFFIC_WORKLOAD.get(args.config))
                 if args.schedule == "fused" else None,

@@ -91,12 +91,13 @@ mst_status mst_destroy(mst_handle h);
  * Runs asynchronously on `stream`.  Returns MST_ERR_INVALID_ARG for negative
  * or too-large sizes, NULL pointers with nonzero sizes, or a NULL handle.
  * Under the default (fused) schedule the solve is one cooperative launch
- * whose CTAs wait on each other at grid barriers.  Two such solves running
- * at the same time on one device (other streams or handles) can each be
- * left partly resident; their barriers then give up after a bounded wait
- * and the solve reports MST_ERR_TIMEOUT.  Order fused solves on one device
- * (one stream, or events), or use the graph schedule for concurrent ones;
- * batched solves and other kernels may run beside a fused solve.
+ * whose CTAs wait on each other at grid barriers, so all of its CTAs must be
+ * resident at once.  The library orders fused solves on one device among
+ * themselves: each waits on its stream for the previous fused solve of the
+ * process on that device (any handle, any stream) to finish, so concurrent
+ * callers are safe; batched solves and other kernels still run beside a
+ * fused solve.  A stream being captured into a CUDA graph is left out of
+ * that ordering, and the caller orders what it replays.
  */
 mst_status mst_solve(mst_handle h, int32_t n, int64_t m,
                      const int32_t *src, const int32_t *dst, const void *w,
@@ -158,7 +159,10 @@ mst_status mst_solve_host(mst_handle h, mst_weight_type wt, int32_t n, int64_t m
                           int32_t *out_edge_ids, int64_t *out_count, void *stream);
 
 /*
- * Minimum spanning trees of G independent graphs in one launch.
+ * Minimum spanning trees of G independent graphs in one launch.  Each graph
+ * gets the Section 2.1 rounds (find-min, union, "covered" edges dropped)
+ * and the tree of Section 1; the batching itself has no counterpart in the
+ * paper, which solves one graph at a time.
  *   vtx_off, edge_off  int64[G+1] device offset tables: graph g has
  *                      n_g = vtx_off[g+1]-vtx_off[g] vertices and edges
  *                      edge_off[g] .. edge_off[g+1]-1 of src/dst/w.
@@ -185,6 +189,22 @@ mst_status mst_solve_batched(mst_handle h, mst_weight_type wt, int32_t G,
  * The status word is cleared at the start of each solve.
  */
 mst_status mst_get_status(mst_handle h, void *stream);
+
+/*
+ * Per-graph outcome of the handle's last batched solve (mst_solve_batched or
+ * mst_autotune_batched); synchronises `stream`.  statuses (host, G entries,
+ * G <= the batch's graph count) receives for each graph the status
+ * mst_get_status would report for a solve of that graph alone: MST_OK,
+ * MST_ERR_DISCONNECTED (forest written), MST_ERR_INVALID_ARG (a bad vertex
+ * id or NaN weight in that graph, or a malformed offset table, which leaves
+ * every graph of the batch unsolved), MST_ERR_INTERNAL.  One graph's bad
+ * input does not change its batch-mates' results or statuses; the combined
+ * status of mst_get_status is the union of all graphs' conditions.
+ * MST_ERR_INVALID_ARG when the last solve on the handle was not batched.
+ * The paper solves one graph at a time (Section 2.1); this is the batched
+ * path's per-graph form of its result.
+ */
+mst_status mst_get_batched_status(mst_handle h, void *stream, int32_t G, int32_t *statuses);
 
 /*
  * Per-round sizes of the handle's last single-graph solve (synchronises
@@ -243,6 +263,20 @@ mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm
                                    int block_threads);
 
 /*
+ * Failure injection for the bounded waits of the default (fused) schedule.
+ * Its CTAs meet at grid barriers whose waits are bounded; a wait that runs
+ * out sets MST_ERR_TIMEOUT in the device status, every CTA leaves the solve
+ * at its next barrier (no phase reads the results of an incomplete one),
+ * *out_count is set to 0, and the handle stays usable.  polls sets how many
+ * polls a barrier wait makes before it gives up (0 restores the default,
+ * 2^22 polls, long enough that only a grid that can never complete gives
+ * up).  A tiny value makes solves time out on purpose, to exercise that
+ * path.  Kept by the handle across workspace growth.  The paper's waits are
+ * lock acquisitions (Section 2.2.1); this library has none, only these.
+ */
+mst_status mst_set_wait_limit(mst_handle h, uint32_t polls);
+
+/*
  * Schedule control for the batched solver (the autotuner's knob).
  * schedule: 0 = automatic (cached autotune result per size bucket, else the
  * built-in default), 1 = one thread block per graph, 2 = one warp per graph
@@ -265,28 +299,33 @@ mst_status mst_autotune_batched(mst_handle h, mst_weight_type wt, int32_t G,
                                 const char *cache_path, void *stream);
 
 /*
- * Allocation-free solve of one small graph, for callers that cannot
- * allocate device memory when they solve: code inside a CUDA graph being
- * captured, hosts that hand out device memory once at start-up, processes
- * whose device memory a framework allocator already holds.  The paper has
- * no counterpart; it is a deployment form of the same rounds.
+ * Allocation-free solve of one small graph.  For callers that cannot
+ * allocate device memory at the point where they solve: a real-time or
+ * plugin host that hands out all of its device memory once at start-up and
+ * must not call the allocator later (cudaMalloc and cudaFree can
+ * synchronise the device and take unbounded time), or a process whose
+ * device memory a framework's caching allocator already holds, so that a
+ * cudaMalloc would fail.  The paper has no counterpart; it is a deployment
+ * form of the same Section 2.1 rounds.
  *   Takes no handle and calls no cudaMalloc, cudaFree or allocating
  *   library routine.  One thread block solves the graph on `stream`, with
  *   its working arrays in shared memory or in a fixed scratch array that the
  *   library declares at file scope: every GPU that loads the library holds
- *   that array (about 5.9 MB) until the process exits.
+ *   that array (6,062,340 bytes) until the process exits.
  *   Limits: n <= 65536 and m <= 262144; larger graphs return MST_ERR_BUDGET
  *   before anything is queued.
  *   Arguments as in mst_solve_ex (device pointers, current device).
  *   out_status: optional device int32 (NULL = none) receiving the device
  *   outcome as an mst_status (MST_OK, MST_ERR_DISCONNECTED,
- *   MST_ERR_INVALID_ARG for a bad vertex id or NaN, MST_ERR_INTERNAL).
+ *   MST_ERR_INVALID_ARG for a bad vertex id or NaN, MST_ERR_TIMEOUT,
+ *   MST_ERR_INTERNAL).
  *   The first call on a device looks up the scratch array's device address
- *   and sets the kernel's shared-memory limit; make that first call outside
- *   any stream capture.  All calls share the one array, which keeps the last
- *   call's contents (the kernel clears what must start empty): calls that
- *   may overlap on the GPU (other streams, other host threads) race on it
- *   and must be serialised by the caller.
+ *   (cudaGetSymbolAddress, with that device current) and sets the kernel's
+ *   shared-memory limit; that first call should come before any stream
+ *   capture.  All calls share the one array, which keeps the last call's
+ *   contents (the kernel clears what must start empty): calls that may
+ *   overlap on the GPU (other streams, other host threads) race on it and
+ *   must be serialised by the caller.
  */
 mst_status mst_solve_noalloc(mst_weight_type wt, int32_t n, int64_t m,
                              const int32_t *src, const int32_t *dst, const void *w,
@@ -296,7 +335,9 @@ mst_status mst_solve_noalloc(mst_weight_type wt, int32_t n, int64_t m,
 /* ---------------------------------------------------------------- serving */
 
 /*
- * Continuous-batching server on top of the batched solver.  A host thread
+ * Continuous-batching server on top of the batched solver (the paper has no
+ * counterpart; each request's result is the Section 1 tree of its graph, as
+ * computed by the Section 2.1 rounds).  A host thread
  * admits submitted graphs under the handle's memory budget, launches each
  * admitted group as one batched solve on one of `streams` CUDA streams, and
  * admits new requests as soon as a stream and memory are free, so solves of

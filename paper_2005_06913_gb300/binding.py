@@ -47,9 +47,11 @@ _SIGS = {
     "mst_profile_last_solve": (_INT, [_P, _P, _P, _I32, ctypes.POINTER(_I32)]),
     "mst_solve_batched": (_INT, [_P, _INT, _I32, _P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P]),
     "mst_get_status": (_INT, [_P, _P]),
+    "mst_get_batched_status": (_INT, [_P, _P, _I32, _P]),
     "mst_get_round_stats": (_INT, [_P, _P, _P, _P, _I32, ctypes.POINTER(_I32)]),
     "mst_set_batched_schedule": (_INT, [_P, _INT, _INT]),
     "mst_set_single_schedule": (_INT, [_P, _INT, _INT, _INT]),
+    "mst_set_wait_limit": (_INT, [_P, ctypes.c_uint32]),
     "mst_autotune_batched": (_INT, [_P, _INT, _I32, _P, _P, _I64, _I64, _P, _P, _P, _P, _P,
                                     ctypes.c_char_p, _P]),
     "mst_solve_noalloc": (_INT, [_INT, _I32, _I64, _P, _P, _P, _P, _P, _P, _P]),
@@ -159,7 +161,7 @@ class KernelProfile(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("alg_bytes", ctypes.c_double)]
 
 
-def mst_profile_last_solve(h, stream=None, cap: int = 16):
+def mst_profile_last_solve(h, stream=None, cap: int = 64):
     """Returns a list of dicts {name, launches, total_ms, alg_bytes}."""
     arr = (KernelProfile * cap)()
     k = _I32(0)
@@ -181,6 +183,13 @@ def mst_get_status(h, stream=None) -> int:
     return lib().mst_get_status(h, _stream(stream))
 
 
+def mst_get_batched_status(h, G: int, stream=None):
+    """Returns (status, per-graph statuses as a list) of the last batched solve."""
+    arr = (_I32 * max(int(G), 1))()
+    st = lib().mst_get_batched_status(h, _stream(stream), int(G), ctypes.addressof(arr))
+    return st, list(arr[: int(G)])
+
+
 def mst_get_round_stats(h, stream=None, cap: int = 65):
     """Returns (live_edges, live_vertices) per round of the last single solve."""
     e = (ctypes.c_int64 * cap)()
@@ -196,6 +205,10 @@ def mst_get_round_stats(h, stream=None, cap: int = 65):
 
 def mst_set_single_schedule(h, schedule: int, blocks_per_sm: int = 0, block_threads: int = 0) -> int:
     return lib().mst_set_single_schedule(h, int(schedule), int(blocks_per_sm), int(block_threads))
+
+
+def mst_set_wait_limit(h, polls: int) -> int:
+    return lib().mst_set_wait_limit(h, int(polls))
 
 
 def mst_set_batched_schedule(h, schedule: int, block_threads: int = 0) -> int:

@@ -17,18 +17,7 @@ double now_us()
     return (double)duration_cast<nanoseconds>(steady_clock::now().time_since_epoch()).count() * 1e-3;
 }
 
-mst_status status_from_bits(uint32_t bits)
-{
-    if (bits & ST_TIMEOUT)
-        return MST_ERR_TIMEOUT;
-    if (bits & ST_INTERNAL)
-        return MST_ERR_INTERNAL;
-    if (bits & (ST_BAD_VERTEX | ST_NAN | ST_BAD_OFFSETS))
-        return MST_ERR_INVALID_ARG;
-    if (bits & ST_DISCONNECTED)
-        return MST_ERR_DISCONNECTED;
-    return MST_OK;
-}
+mst_status status_from_bits(uint32_t bits) { return status_code(bits); }
 
 static mst_status cuda_status(cudaError_t e)
 {
@@ -407,6 +396,24 @@ mst_status mst_get_status(mst_handle h, void *stream)
     return MST_OK;
 }
 
+mst_status mst_get_batched_status(mst_handle h, void *stream, int32_t G, int32_t *statuses)
+{
+    if (!h || G < 0 || (G > 0 && !statuses))
+        return MST_ERR_INVALID_ARG;
+    if (G == 0)
+        return MST_OK;
+    if (h->last != LAST_BATCHED || G > h->batched.last_G || !h->batched.base)
+        return MST_ERR_INVALID_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess)
+        return MST_ERR_CUDA;
+    std::vector<uint32_t> bits((size_t)G);
+    if (batched_graph_status(h->batched, (cudaStream_t)stream, G, bits.data()) != cudaSuccess)
+        return MST_ERR_CUDA;
+    for (int32_t g = 0; g < G; g++)
+        statuses[g] = (int32_t)status_from_bits(bits[(size_t)g]);
+    return MST_OK;
+}
+
 mst_status mst_get_round_stats(mst_handle h, void *stream, int64_t *live_edges,
                                int64_t *live_vertices, int32_t cap, int32_t *rounds)
 {
@@ -497,6 +504,14 @@ mst_status mst_set_single_schedule(mst_handle h, int schedule, int blocks_per_sm
         single_release(h->single);  // the grid is fixed at reservation time
         h->last_solve.valid = false;
     }
+    return MST_OK;
+}
+
+mst_status mst_set_wait_limit(mst_handle h, uint32_t polls)
+{
+    if (!h)
+        return MST_ERR_INVALID_ARG;
+    h->single.wait_limit = polls;
     return MST_OK;
 }
 

@@ -49,6 +49,7 @@ struct BWs {
     int32_t *parent, *nid, *lab;
     uint32_t *bits;             // total_m/32 + G + 1 words
     int32_t *order;             // G
+    uint32_t *gstat;            // G: status bits of each graph's own solve
     uint64_t total_n, total_m;
 };
 
@@ -757,6 +758,7 @@ __global__ void k_b_prep(BWs ws, BJob job, uint64_t total_n, uint64_t total_m)
         }
         if (bad)
             atomicOr(&c->status, ST_BAD_OFFSETS);
+        ws.gstat[g] = bad ? ST_BAD_OFFSETS : 0u;
         const uint32_t m = bad ? 0u : gv.m;
         const uint32_t bin = m ? 31u - __clz(m) : 0u;
         const bool big = job.warp_max_m == 0 || m > job.warp_max_m;
@@ -784,8 +786,20 @@ __global__ void k_b_order(BWs ws, BJob job)
         const uint32_t b = bin + (big ? 32 : 0);
         if (gv.out_count)
             *gv.out_count = 0;
+        if (c->status & ST_BAD_OFFSETS)  // nothing of this batch is solved
+            ws.gstat[g] = ST_BAD_OFFSETS;
         ws.order[base[b] + atomicAdd(&c->bin_cursor[b], 1u)] = g;
     }
+}
+
+// Records the status bits of graph g's solve (kept in the team's shared
+// memory while it runs, so a graph's outcome never reaches its batch-mates)
+// and adds them to the batch's combined status word.
+__device__ __forceinline__ void publish_status(const BWs &ws, int g, uint32_t bits)
+{
+    ws.gstat[g] = bits;
+    if (bits)
+        atomicOr(&ws.ctl->status, bits);
 }
 
 template <int T>
@@ -794,7 +808,7 @@ __global__ void __launch_bounds__(T) k_b_solve(BWs ws, BJob job)
     extern __shared__ __align__(16) char smem[];
     __shared__ uint32_t scratch[4 * (T / 32) + 2];
     __shared__ unsigned long long ring[kRing];
-    __shared__ uint32_t s_claim, s_total;
+    __shared__ uint32_t s_claim, s_total, s_gstat, s_wstat[T / 32];
     BCtl *c = ws.ctl;
     if (c->status & ST_BAD_OFFSETS)
         return;
@@ -814,8 +828,12 @@ __global__ void __launch_bounds__(T) k_b_solve(BWs ws, BJob job)
         const int g = ws.order[q];
         const GraphView gv = graph_at(job, g);
         const GraphArrays A = place(ws, smem, job.smem_bytes, g, gv.vo, gv.eo, gv.n, gv.m);
+        if (threadIdx.x == 0)
+            s_gstat = 0u;  // ordered before any use by the solver's first team barrier
         solve_graph(team, gv.n, gv.m, gv.src, gv.dst, gv.w, gv.wt, A, gv.out, gv.out_count,
-                    &c->status);
+                    &s_gstat);
+        if (threadIdx.x == 0)
+            publish_status(ws, g, *(volatile uint32_t *)&s_gstat);
     }
     if (job.warp_max_m == 0)
         return;
@@ -835,8 +853,13 @@ __global__ void __launch_bounds__(T) k_b_solve(BWs ws, BJob job)
         const int g = ws.order[q];
         const GraphView gv = graph_at(job, g);
         const GraphArrays A = place(ws, mine, share, g, gv.vo, gv.eo, gv.n, gv.m);
+        if (lane == 0)
+            s_wstat[warp] = 0u;
+        __syncwarp();
         solve_graph(wt_team, gv.n, gv.m, gv.src, gv.dst, gv.w, gv.wt, A, gv.out, gv.out_count,
-                    &c->status);
+                    &s_wstat[warp]);
+        if (lane == 0)
+            publish_status(ws, g, *(volatile uint32_t *)&s_wstat[warp]);
     }
 }
 
@@ -858,7 +881,7 @@ size_t batched_bytes(int32_t G, uint64_t n, uint64_t m)
     b += al256(n * 16);
     b += 3 * al256(n * 4);
     b += al256((m / 32 + (uint64_t)G + 1) * 4);
-    b += al256((size_t)G * 4);
+    b += 2 * al256((size_t)G * 4);  // order, per-graph status
     return b;
 }
 
@@ -912,6 +935,7 @@ static BWs carve_at(void *base, int32_t g_cap, uint64_t n_cap, uint64_t m_cap, u
     ws.lab = (int32_t *)take(n_cap * 4);
     ws.bits = (uint32_t *)take((m_cap / 32 + (uint64_t)g_cap + 1) * 4);
     ws.order = (int32_t *)take((size_t)g_cap * 4);
+    ws.gstat = (uint32_t *)take((size_t)g_cap * 4);
     ws.total_n = total_n;
     ws.total_m = total_m;
     return ws;
@@ -934,6 +958,7 @@ static BWs carve(Batched &b, uint64_t total_n, uint64_t total_m)
     ws.lab = (int32_t *)take(b.n_cap * 4);
     ws.bits = (uint32_t *)take((b.m_cap / 32 + (uint64_t)b.g_cap + 1) * 4);
     ws.order = (int32_t *)take((size_t)b.g_cap * 4);
+    ws.gstat = (uint32_t *)take((size_t)b.g_cap * 4);
     ws.total_n = total_n;  // mins B half starts after the batch's vertices
     ws.total_m = total_m;
     return ws;
@@ -979,6 +1004,7 @@ static cudaError_t run_batched(Batched &b, int device, const BWs &ws, BJob job, 
 {
     job.warp_max_m = ch.warp_max_m;
     job.smem_bytes = smem_for(device, ch.blocks_per_sm);
+    b.last_G = job.G;
     MST_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(BCtl), s));
     const int pg = (int)std::min<int64_t>((job.G + 255) / 256, 1024);
     k_b_prep<<<std::max(pg, 1), 256, 0, s>>>(ws, job, ws.total_n, ws.total_m);
@@ -1103,6 +1129,22 @@ cudaError_t desc_batch_status(void *ws_base, uint32_t *bits, cudaStream_t stream
     return cudaStreamSynchronize(stream);
 }
 
+cudaError_t desc_batch_graph_status(void *ws_base, int32_t G, uint64_t total_n, uint64_t total_m,
+                                    uint32_t *bits)
+{
+    const BWs ws = carve_at(ws_base, G, total_n, total_m, total_n, total_m);
+    return cudaMemcpy(bits, ws.gstat, (size_t)G * 4, cudaMemcpyDeviceToHost);
+}
+
+cudaError_t batched_graph_status(Batched &b, cudaStream_t stream, int32_t G, uint32_t *bits)
+{
+    if (!b.base || G > b.last_G)
+        return cudaErrorInvalidValue;
+    const BWs ws = carve(b, 0, 0);
+    MST_TRY(cudaStreamSynchronize(stream));
+    return cudaMemcpy(bits, ws.gstat, (size_t)G * 4, cudaMemcpyDeviceToHost);
+}
+
 uint32_t batched_status_bits(Batched &b, cudaStream_t stream, cudaError_t *err)
 {
     *err = cudaSuccess;
@@ -1172,11 +1214,11 @@ cudaError_t batched_autotune(Batched &b, int device, uint32_t wt, int32_t G,
 
 // ------------------------------------------------- allocation-free solve
 
-// Some callers cannot allocate device memory at solve time: code running
-// inside a CUDA graph being captured, a real-time or plugin host whose
-// memory is handed out once at start-up, or a process whose device memory
-// is fully reserved by a framework allocator.  mst_solve_noalloc serves
-// them: one CTA runs every Boruvka round of one graph (the batched solver's
+// Some callers cannot allocate device memory at solve time: a real-time or
+// plugin host whose device memory is handed out once at start-up (the
+// allocator may synchronise the device and take unbounded time), or a
+// process whose device memory a framework's caching allocator already
+// holds.  mst_solve_noalloc serves them: one CTA runs every Boruvka round of one graph (the batched solver's
 // per-graph team), with its working arrays in this file-scope device array
 // instead of a handle's workspace.  Every GPU that loads the library holds
 // the array until the process exits; every call shares it and it keeps the
@@ -1189,6 +1231,7 @@ constexpr size_t kNoAllocEdgeBytes = (size_t)kNoAllocMaxM * 16;
 constexpr size_t kNoAllocVtxBytes = 2 * (size_t)kNoAllocMaxN * 8 + 3 * (size_t)kNoAllocMaxN * 4;
 constexpr size_t kNoAllocBitsBytes = ((size_t)kNoAllocMaxM / 32 + 1) * 4;
 constexpr size_t kNoAllocBytes = 256 + kNoAllocEdgeBytes + kNoAllocVtxBytes + kNoAllocBitsBytes;
+static_assert(kNoAllocBytes == 6062340, "the byte count documented in mst.h");
 constexpr int kNoAllocThreads = 1024;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1235,17 +1278,8 @@ k_noalloc(unsigned char *scratch, uint32_t smem_bytes, const int32_t *src, const
     BlockTeam<kNoAllocThreads> team{scratch_words, ring, &s_total};
     const GraphArrays A = place_noalloc(scratch, smem, smem_bytes, n, m);
     solve_graph(team, n, m, src, dst, w, wt, A, out, out_count, status);
-    if (threadIdx.x == 0 && out_status) {
-        const uint32_t b = *(volatile uint32_t *)status;
-        int32_t code = MST_OK;
-        if (b & ST_INTERNAL)
-            code = MST_ERR_INTERNAL;
-        else if (b & (ST_BAD_VERTEX | ST_NAN))
-            code = MST_ERR_INVALID_ARG;
-        else if (b & ST_DISCONNECTED)
-            code = MST_ERR_DISCONNECTED;
-        *out_status = code;
-    }
+    if (threadIdx.x == 0 && out_status)
+        *out_status = (int32_t)status_code(*(volatile uint32_t *)status);
 }
 
 // Device address of the scratch array, looked up once per device with that

@@ -83,6 +83,9 @@ struct Ctl {
     uint32_t tail_cnt[kMaxRounds + 2];  // tail edge-list lengths (fused schedule)
     uint32_t tail_nn[kMaxRounds + 2];   // components after each tail round
     uint32_t tail_added;                // tree edges the tail added
+    uint32_t tick_find0;                // tile tickets of the fused kernel's balanced phases
+    uint32_t tick_hook[kMaxRounds + 2];
+    uint32_t tick_comp[kMaxRounds + 2];
     uint32_t nphase;  // entries used in the phase log (fused schedule)
     uint8_t phase_kind[kMaxPhaseLog];
     uint8_t phase_round[kMaxPhaseLog];

@@ -19,6 +19,22 @@
 
 namespace mst {
 
+// The status a solve reports for a set of device status bits (host and
+// device): a bounded wait that gave up outranks everything, then an internal
+// check, then bad input, then a disconnected graph.
+__host__ __device__ inline mst_status status_code(uint32_t bits)
+{
+    if (bits & ST_TIMEOUT)
+        return MST_ERR_TIMEOUT;
+    if (bits & ST_INTERNAL)
+        return MST_ERR_INTERNAL;
+    if (bits & (ST_BAD_VERTEX | ST_NAN | ST_BAD_OFFSETS))
+        return MST_ERR_INVALID_ARG;
+    if (bits & ST_DISCONNECTED)
+        return MST_ERR_DISCONNECTED;
+    return MST_OK;
+}
+
 // ------------------------------------------------------------ single graph
 
 // Workspace and captured round loop of the single-graph solver.
@@ -36,6 +52,7 @@ struct Single {
     int schedule = 0;       // 0 fused, shape per solve; 1 fused, fixed shape; 2 CUDA graph
     int sms = 0;            // multiprocessors of the device
     uint64_t solves = 0;    // solves since the descriptors were last cleared
+    uint32_t wait_limit = 0;  // polls of a grid-barrier wait before it gives up (0: default)
 };
 
 struct KernelProfile {
@@ -105,6 +122,7 @@ struct Batched {
     int block_threads = 0;  // forced block size (0 = autotuned/default)
     std::map<int, BatchedConfig> tuned;  // size bucket -> choice
     bool tuned_loaded = false;
+    int32_t last_G = 0;     // graphs of the last batched launch (per-graph status)
 };
 
 size_t batched_bytes(int32_t G, uint64_t n, uint64_t m);
@@ -115,6 +133,11 @@ cudaError_t batched_launch(Batched &b, int device, uint32_t wt, int32_t G, const
                            const int32_t *src, const int32_t *dst, const void *w, int32_t *out,
                            int64_t *out_counts, cudaStream_t stream);
 uint32_t batched_status_bits(Batched &b, cudaStream_t stream, cudaError_t *err);
+// Status bits of each graph of the last batched launch (synchronises `stream`).
+cudaError_t batched_graph_status(Batched &b, cudaStream_t stream, int32_t G, uint32_t *bits);
+// Status bits of each graph of a finished descriptor batch run in `ws_base`.
+cudaError_t desc_batch_graph_status(void *ws_base, int32_t G, uint64_t total_n, uint64_t total_m,
+                                    uint32_t *bits);
 // Workspace bytes of a descriptor batch with these totals.
 size_t desc_batch_bytes(int32_t G, uint64_t total_n, uint64_t total_m);
 // Solves a descriptor batch in caller-provided workspace `ws_base` (of

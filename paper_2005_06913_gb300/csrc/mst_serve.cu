@@ -43,6 +43,7 @@ struct Slot {
     int cap = 0;
     void *ws = nullptr;           // workspace of the batch in flight
     size_t ws_bytes = 0;
+    uint64_t total_n = 0, total_m = 0;  // the batch's totals (locate per-graph status)
     std::vector<uint64_t> tickets;
     bool busy = false;
 };
@@ -80,23 +81,30 @@ static size_t request_bytes(uint32_t n, uint32_t m)
     return (size_t)m * 16 + (size_t)n * 28 + ((size_t)m / 32 + 2) * 4 + 64;
 }
 
+// Each request gets the status of its own solve, as mst_solve_ex would
+// report it for that graph alone (a forest is MST_ERR_DISCONNECTED, a bad
+// vertex id or NaN weight MST_ERR_INVALID_ARG), never a batch-mate's.
 static void complete_slot(Server &S, Slot &sl)
 {
     const double t = now_us();
-    uint32_t bits = 0;
+    std::vector<uint32_t> bits(sl.tickets.size(), 0u);
+    cudaError_t e = cudaSuccess;
     if (sl.big) {
-        cudaMemcpy(&bits, &S.lane.ws.ctl->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(bits.data(), &S.lane.ws.ctl->status, sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost);
     } else {
-        cudaMemcpy(&bits, sl.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        if (!bits.empty())
+            e = desc_batch_graph_status(sl.ws, (int32_t)bits.size(), sl.total_n, sl.total_m,
+                                        bits.data());
         cudaFreeAsync(sl.ws, sl.stream);
     }
-    const mst_status st = status_from_bits(bits & ~(uint32_t)ST_DISCONNECTED);
     std::lock_guard<std::mutex> lk(S.mu);
-    for (uint64_t tk : sl.tickets) {
+    for (size_t i = 0; i < sl.tickets.size(); i++) {
+        const uint64_t tk = sl.tickets[i];
         Outcome &o = S.results[tk];
         o.done = true;
         o.latency_us = t - S.submit_us[tk];
-        o.status = st;
+        o.status = e != cudaSuccess ? MST_ERR_CUDA : status_from_bits(bits[i]);
         S.submit_us.erase(tk);
     }
     if (!sl.big)
@@ -272,6 +280,8 @@ static cudaError_t launch_batch(Server &S, Slot &sl, std::vector<Request> &batch
     if (e != cudaSuccess)
         return e;
     sl.ws_bytes = bytes;
+    sl.total_n = vo;
+    sl.total_m = eo;
     e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(GraphDesc) * G, cudaMemcpyHostToDevice,
                         sl.stream);
     if (e == cudaSuccess)

@@ -112,45 +112,121 @@ __device__ __forceinline__ void store4_soa(int32_t *csrc, int32_t *cdst, uint32_
     }
 }
 
-// Round-0 find-min over edge groups [g0, groups) step gstep (4 edges each).
+// Round-0 find-min of one group of 4 edges starting at e0.  Its keys are
+// (weight_bits << 32) | (edge id << 1) | side: edge ids are below 2^31, and
+// the side bit (0: offered to src, 1: to dst) only rides along, since one
+// edge offers once to each endpoint, so the order is still (weight, edge
+// id); the hook then reads only the endpoint across from the component.
 // With csrc non-null the inputs are read from mapped host memory and also
 // copied to device memory (csrc, cdst, cw), which the later phases read.
+__device__ __forceinline__ void find0_group(unsigned long long *mn, const int32_t *src,
+                                            const int32_t *dst, const uint32_t *w, uint32_t n,
+                                            uint32_t m, uint32_t wt, uint32_t vec,
+                                            uint32_t *status, bool filtered, uint32_t e0,
+                                            int32_t *csrc, int32_t *cdst, uint32_t *cw)
+{
+    int32_t us[4], vs[4];
+    uint32_t wr[4];
+    load4_soa(src, dst, w, e0, m, vec, us, vs, wr);
+    if (csrc)
+        store4_soa(csrc, cdst, cw, e0, m, us, vs, wr);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (e0 + j >= m)
+            continue;
+        const uint32_t u = (uint32_t)us[j], v = (uint32_t)vs[j];
+        if (u >= n || v >= n) {
+            atomicOr(status, ST_BAD_VERTEX);
+            continue;
+        }
+        if (u == v)
+            continue;
+        const unsigned long long key = make_key(weight_bits(wr[j], wt, status), (e0 + j) << 1);
+        if (filtered) {
+            offer_min(&mn[u], key);
+            offer_min(&mn[v], key | 1ull);
+        } else {
+            red_min_u64(&mn[u], key);
+            red_min_u64(&mn[v], key | 1ull);
+        }
+    }
+}
+
+// Round-0 find-min over edge groups [g0, groups) step gstep.
 __device__ __forceinline__ void find0_range(const Ws &ws, const int32_t *src, const int32_t *dst,
                                             const uint32_t *w, uint32_t n, uint32_t m, uint32_t wt,
                                             uint32_t vec, uint32_t *status, size_t g0,
                                             size_t gstep, int32_t *csrc = nullptr,
                                             int32_t *cdst = nullptr, uint32_t *cw = nullptr)
 {
-    unsigned long long *mn = ws.mins[0];
     const size_t groups = ((size_t)m + 3) >> 2;
     const bool filtered = use_filter(m, n);
-    for (size_t g = g0; g < groups; g += gstep) {
-        const uint32_t e0 = (uint32_t)(g << 2);
-        int32_t us[4], vs[4];
-        uint32_t wr[4];
-        load4_soa(src, dst, w, e0, m, vec, us, vs, wr);
-        if (csrc)
-            store4_soa(csrc, cdst, cw, e0, m, us, vs, wr);
+    for (size_t g = g0; g < groups; g += gstep)
+        find0_group(ws.mins[0], src, dst, w, n, m, wt, vec, status, filtered, (uint32_t)(g << 2),
+                    csrc, cdst, cw);
+}
+
+// Round-0 find-min of one warp tile: kFind0Groups groups of 4 edges, lane l
+// taking groups l, l + 32, ... of the tile (each load of the warp contiguous).
+constexpr uint32_t kFind0Groups = 64;
+constexpr uint32_t kFind0WTile = 4 * kFind0Groups;  // edges
+
+__device__ __forceinline__ void find0_wtile(const Ws &ws, const int32_t *src, const int32_t *dst,
+                                            const uint32_t *w, uint32_t n, uint32_t m, uint32_t wt,
+                                            uint32_t vec, uint32_t *status, bool filtered,
+                                            uint32_t tile, int32_t *csrc, int32_t *cdst,
+                                            uint32_t *cw)
+{
+    const uint32_t lane = threadIdx.x & 31;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (e0 + j >= m)
-                continue;
-            const uint32_t u = (uint32_t)us[j], v = (uint32_t)vs[j];
-            if (u >= n || v >= n) {
-                atomicOr(status, ST_BAD_VERTEX);
-                continue;
-            }
-            if (u == v)
-                continue;
-            const unsigned long long key = make_key(weight_bits(wr[j], wt, status), e0 + j);
-            if (filtered) {
-                offer_min(&mn[u], key);
-                offer_min(&mn[v], key);
-            } else {
-                red_min_u64(&mn[u], key);
-                red_min_u64(&mn[v], key);
-            }
-        }
+    for (uint32_t j = 0; j < kFind0Groups / 32; j++) {
+        const uint32_t e0 = tile * kFind0WTile + (j * 32 + lane) * 4;
+        if (e0 < m)
+            find0_group(ws.mins[0], src, dst, w, n, m, wt, vec, status, filtered, e0, csrc,
+                        cdst, cw);
+    }
+}
+
+// Runs body(t) for the warp tiles t < ntiles of a phase, balanced between
+// warps.  The first kStaticShare of a warp's fair share is static (global
+// warp gw takes tiles gw, gw + nw, ...); the rest of the tiles go to whichever
+// warp asks next, from the phase's counter *ctr, so warps that drew slow
+// tiles do not hold the phase's end.  A ticket is taken before the current
+// tile's work, so its latency overlaps that work; a warp that draws a tile
+// past the end leaves.  Every tile runs exactly once.  (All tiles from the
+// counter made one address the bottleneck of the round-0 find-min: ~300 M
+// tickets/s; with a quarter of them, the counter is no longer felt.)
+constexpr uint32_t kStaticShareNum = 3, kStaticShareDen = 4, kDynMinShare = 4;
+
+template <typename F>
+__device__ __forceinline__ void for_warp_tiles(uint32_t *ctr, uint32_t ntiles, uint32_t gw,
+                                               uint32_t nw, F &&body)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    // phases of fewer than kDynMinShare tiles per warp stay static: each warp
+    // has too few tiles to balance, and a ticket's round trip would only
+    // lengthen the phase (measured on the 1024 x 1024 grid's late rounds)
+    const bool small = (unsigned long long)ntiles < (unsigned long long)kDynMinShare * nw;
+    const uint32_t k_static =
+        small ? (ntiles + nw - 1) / nw
+              : (uint32_t)((unsigned long long)ntiles * kStaticShareNum /
+                           ((unsigned long long)nw * kStaticShareDen));
+    const uint32_t dyn0 = k_static * nw;  // tiles before this one are static
+    // tile k of this warp: gw + k*nw while k < k_static, then dyn0 + gw (still
+    // fixed), then dyn0 + nw + a ticket (one loop, so the body is inlined once)
+    uint32_t k = 0, t = k_static ? gw : dyn0 + gw;
+    while (t < ntiles) {
+        uint32_t nx = 0;
+        if (lane == 0 && k >= k_static)
+            nx = atomicAdd(ctr, 1u);
+        body(t);
+        k++;
+        if (k < k_static)
+            t = gw + k * nw;
+        else if (k == k_static)
+            t = dyn0 + gw;
+        else
+            t = __shfl_sync(0xffffffffu, nx, 0) + dyn0 + nw;
     }
 }
 
@@ -192,10 +268,11 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
         a[j] = b[j] = id[j] = 0;
         if (k[j] != kNoEdge) {
             const uint32_t p = (uint32_t)k[j];
-            if (R0) {
-                a[j] = (uint32_t)__ldg(src + p);
-                b[j] = (uint32_t)__ldg(dst + p);
-                id[j] = p;
+            if (R0) {  // one gather: the endpoint across from v (side bit of the key)
+                const uint32_t e = p >> 1;
+                a[j] = (uint32_t)__ldg(((p & 1u) ? src : dst) + e);
+                b[j] = a[j];
+                id[j] = e;
             } else {
                 const uint2 r = __ldcg(ws.eends + p);
                 a[j] = r.x;
@@ -211,6 +288,10 @@ __device__ __forceinline__ void hook_wtile(const Ws &ws, Ctl *c, uint32_t tile, 
         const uint32_t d = (a[j] == v) ? b[j] : a[j];
         a[j] = d;  // a now holds the other component
         kd[j] = k[j] != kNoEdge ? mcur[d] : kNoEdge;
+        if (R0) {  // compare edge ids: the two sides of one edge differ in the side bit
+            kd[j] >>= 1;
+            k[j] = k[j] == kNoEdge ? kNoEdge : k[j] >> 1;
+        }
     }
     uint32_t mask[kHookIpl], total = 0;
 #pragma unroll
@@ -301,11 +382,12 @@ __device__ __forceinline__ void hook_cas_wtile(const Ws &ws, Ctl *c, uint32_t ti
         mnext[v] = kNoEdge;
         if (k == kNoEdge)
             continue;
-        const uint32_t p = (uint32_t)k;
+        uint32_t p = (uint32_t)k;
         uint32_t a, b;
-        if (R0) {
-            a = (uint32_t)__ldg(src + p);
-            b = (uint32_t)__ldg(dst + p);
+        if (R0) {  // the round-0 key carries a side bit below the edge id
+            p >>= 1;
+            a = v;
+            b = (uint32_t)__ldg((((uint32_t)k & 1u) ? src : dst) + p);
         } else {
             const uint2 e = __ldcg(ws.eends + p);
             a = e.x;
@@ -764,25 +846,34 @@ __device__ __forceinline__ void finish(Ctl *c, int64_t *out_count, uint32_t emit
 // bit flips exactly when the last block arrives and its low bits return to
 // where they were; each block spins until the top bit differs from the
 // value it saw when it arrived.  One atomic per block, nothing to reset.
-// Waits are bounded: on expiry ST_TIMEOUT is set and later barriers no
-// longer wait.
+// Waits are bounded (spin_limit polls; 0 means kBarSpinLimit): on expiry
+// ST_TIMEOUT is set, later barriers no longer wait, and the barrier tells
+// every thread of the CTA to abandon the solve.
 constexpr uint32_t kBarCount = 0;
 constexpr uint32_t kBarSpinLimit = 1u << 22;
 
-// Barrier among CTAs [0, nb) (all co-resident); `slot` picks the counter.
-__device__ __forceinline__ void team_sync(uint32_t *counter, uint32_t nb, uint32_t *status)
+// Barrier among CTAs [0, nb) (all co-resident).  Returns true in every
+// thread of the CTA when the solve has timed out (this CTA's wait ran out,
+// or another CTA's did before): the data of the phase just ended may then
+// be incomplete, so the caller must not start the next phase.  The verdict
+// is read once by thread 0 and broadcast, so a CTA never splits on it.
+__device__ __forceinline__ bool team_sync(uint32_t *counter, uint32_t nb, uint32_t *status,
+                                          uint32_t spin_limit)
 {
+    __shared__ uint32_t s_abort;
     __syncthreads();
     if (threadIdx.x == 0) {
+        const uint32_t limit = spin_limit ? spin_limit : kBarSpinLimit;
         const uint32_t inc = blockIdx.x == 0 ? 0x80000000u - (nb - 1) : 1u;
         __threadfence();
         const uint32_t old = atomicAdd(counter, inc);
         uint32_t spins = 0;
         while (((old ^ ld_volatile_u32(counter)) & 0x80000000u) == 0) {
-            if (++spins > kBarSpinLimit) {
+            if (++spins > limit) {
                 atomicOr(status, ST_TIMEOUT);
-                printf("mst: grid barrier gave up: block %u of %u, arrival value %u, now %u\n",
-                       blockIdx.x, nb, old, ld_volatile_u32(counter));
+                if (!spin_limit)  // a real give-up, not an injected short limit
+                    printf("mst: grid barrier gave up: block %u of %u, arrival value %u, now %u\n",
+                           blockIdx.x, nb, old, ld_volatile_u32(counter));
                 break;
             }
             if (ld_volatile_u32(status) & ST_TIMEOUT)
@@ -791,14 +882,17 @@ __device__ __forceinline__ void team_sync(uint32_t *counter, uint32_t nb, uint32
                 __nanosleep(32);
         }
         __threadfence();
+        s_abort = (ld_volatile_u32(status) & ST_TIMEOUT) ? 1u : 0u;
     }
     __syncthreads();
+    return s_abort != 0u;
 }
 
-__device__ __forceinline__ void grid_sync(uint32_t *bar, uint32_t &gen, uint32_t *status)
+__device__ __forceinline__ bool grid_sync(uint32_t *bar, uint32_t &gen, uint32_t *status,
+                                          uint32_t spin_limit)
 {
-    team_sync(bar + kBarCount, gridDim.x, status);
     gen++;
+    return team_sync(bar + kBarCount, gridDim.x, status, spin_limit);
 }
 
 constexpr uint32_t kBarTeam = 32;  // counter of the tail's sub-grid team (own 128-B line)
@@ -969,7 +1063,7 @@ constexpr uint32_t kTailEdgesPerThread = 4;  // swept 2..64: 4 is fastest on sma
 
 template <int kFT>
 __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, uint32_t r_base,
-                            TileSmem &sm)
+                            TileSmem &sm, uint32_t spin_limit)
 {
     const uint32_t bid = blockIdx.x;
     const uint32_t n_t = n_r;
@@ -1005,9 +1099,11 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
             local = true;
         }
         team_prev = team;
+        bool aborted = false;  // a team barrier ran out: leave (the grid barrier after
+                               // the tail then sees the timeout and ends the solve)
         auto sync = [&]() {
             if (team > 1)
-                team_sync(ws.bar + kBarTeam, team, &c->status);
+                aborted = aborted || team_sync(ws.bar + kBarTeam, team, &c->status, spin_limit);
             else
                 __syncthreads();
         };
@@ -1042,6 +1138,8 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
             }
         }
         sync();
+        if (aborted)
+            return;
         // roots: full path compression (any pointer value read is an
         // ancestor); roots take dense new ids
         uint32_t *nn = &c->tail_nn[tr];
@@ -1059,6 +1157,8 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
                 tpar[v] = (int32_t)x;
         }
         sync();
+        if (aborted)
+            return;
         const uint32_t n_next = ld_volatile_u32(nn);
         // merge: relabel, offer to the pair slot; first writers record slots
         uint32_t *touched = &c->tail_cnt[tr + 1];
@@ -1082,6 +1182,8 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
         for (size_t v = tid; v < n_next; v += nthr)
             tmin[v] = kNoEdge;
         sync();
+        if (aborted)
+            return;
         // next list: the recorded slots, reset; find-min of the next round
         const uint32_t m_next = ld_volatile_u32(touched);
         for (size_t i = tid; i < m_next; i += nthr) {
@@ -1101,6 +1203,8 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
         for (size_t v = tid; v < n_next; v += nthr)
             tpar[v] = (int32_t)v;
         sync();
+        if (aborted)
+            return;
         if (bid == 0 && threadIdx.x == 0 && r_base + tr + 1 <= (uint32_t)kMaxRounds) {
             c->stat_m[r_base + tr + 1] = m_next;
             c->stat_n[r_base + tr + 1] = n_next;
@@ -1108,8 +1212,6 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
         m_r = m_next;
         n_r = n_next;
         cur ^= 1;
-        if (team > 1 && (ld_volatile_u32(&c->status) & ST_TIMEOUT))
-            break;
     }
     if (bid == 0 && threadIdx.x == 0)
         c->tail_added = n_t - n_r;
@@ -1125,7 +1227,7 @@ template <int kFT>
 __global__ void __launch_bounds__(kFT, 1024 / kFT)
 k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_t *out,
         int64_t *out_count, uint32_t n, uint32_t m, uint32_t wt, uint32_t vec, int32_t *csrc,
-        int32_t *cdst, uint32_t *cw, uint32_t variant)
+        int32_t *cdst, uint32_t *cw, uint32_t variant, uint32_t spin_limit)
 {
     const bool covered = (variant & kVariantCovered) != 0, cas = (variant & kVariantCas) != 0;
     constexpr int kFW = kFT / 32;
@@ -1136,6 +1238,18 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
     const size_t gtid = (size_t)bid * kFT + threadIdx.x, gstride = (size_t)nb * kFT;
     const uint32_t gw = bid * kFW + (threadIdx.x >> 5), nw = nb * kFW;  // global warp
     uint32_t gen = 0;  // barrier count (the barrier itself keeps no generation)
+// Every grid barrier of the solve: when a bounded wait has run out (here or
+// in another CTA), the phase just ended may be incomplete, so the CTA stops
+// before reading its results; no later index can then leave its buffer.
+// The status word keeps ST_TIMEOUT and the count of written ids is 0.
+#define MST_SYNC_OR_ABORT()                               \
+    do {                                                  \
+        if (grid_sync(ws.bar, gen, status, spin_limit)) { \
+            if (gtid == 0)                                \
+                *out_count = 0;                           \
+            return;                                       \
+        }                                                 \
+    } while (0)
     log_phase(c, PH_START);
     init_range(ws, n, m, gtid, gstride);
     if (cas)  // the CAS hook swaps roots' pointers: every component starts as one
@@ -1153,11 +1267,18 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         c->stat_m[0] = m;
         c->stat_n[0] = n;
     }
-    grid_sync(ws.bar, gen, status);
+    MST_SYNC_OR_ABORT();
     log_phase(c, PH_INIT);
-    find0_range(ws, src, dst, w, n, m, wt, vec, status, gtid, gstride, csrc, cdst, cw);
+    {
+        const bool filtered = use_filter(m, n);
+        for_warp_tiles(&c->tick_find0, (m + kFind0WTile - 1) / kFind0WTile, gw, nw,
+                       [&](uint32_t t) {
+                           find0_wtile(ws, src, dst, w, n, m, wt, vec, status, filtered, t, csrc,
+                                       cdst, cw);
+                       });
+    }
     mark_work(c);
-    grid_sync(ws.bar, gen, status);
+    MST_SYNC_OR_ABORT();
     log_phase(c, PH_FIND0);
     if (csrc) {  // host inputs: the later phases read the device copy
         src = csrc;
@@ -1172,26 +1293,30 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         const uint32_t nth = (n_cur + kHookWTile - 1) / kHookWTile;
         if (bid == 0 && threadIdx.x == 0)
             c->flag3[0] = 0;
-        for (uint32_t t = gw; t < nth; t += nw) {
-            if (cas) {
+        if (cas) {
+            for (uint32_t t = gw; t < nth; t += nw) {
                 if (r == 0)
                     hook_cas_wtile<true>(ws, c, t, r, n_cur, src, dst);
                 else
                     hook_cas_wtile<false>(ws, c, t, r, n_cur, src, dst);
-            } else if (r == 0) {
-                hook_wtile<true>(ws, c, t, r, n_cur, src, dst);
-            } else {
-                hook_wtile<false>(ws, c, t, r, n_cur, src, dst);
             }
+        } else if (r == 0) {
+            for_warp_tiles(&c->tick_hook[r], nth, gw, nw, [&](uint32_t t) {
+                hook_wtile<true>(ws, c, t, r, n_cur, src, dst);
+            });
+        } else {
+            for_warp_tiles(&c->tick_hook[r], nth, gw, nw, [&](uint32_t t) {
+                hook_wtile<false>(ws, c, t, r, n_cur, src, dst);
+            });
         }
         mark_work(c);
-        grid_sync(ws.bar, gen, status);
+        MST_SYNC_OR_ABORT();
         log_phase(c, PH_HOOK, r);
         if (cas) {
             for (uint32_t t = gw; t < nth; t += nw)
                 number_roots_wtile(ws, c, t, r, n_cur);
             mark_work(c);
-            grid_sync(ws.bar, gen, status);
+            MST_SYNC_OR_ABORT();
             log_phase(c, PH_ROOTS, r);
         }
         const uint32_t n_next = ld_volatile_u32(&c->cnt_n[r]);
@@ -1213,7 +1338,7 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             if (__syncthreads_or(unf ? 1 : 0) && threadIdx.x == 0)
                 c->flag3[pass % 3] = 1u;
             mark_work(c);
-            grid_sync(ws.bar, gen, status);
+            MST_SYNC_OR_ABORT();
             log_phase(c, PH_COMPRESS, r);
             if (!ld_volatile_u32(&c->flag3[pass % 3]))
                 break;
@@ -1225,28 +1350,28 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         }
         if (tail) {
             const uint32_t ntp = (m_cur + kCompWTile - 1) / kCompWTile;
-            for (uint32_t t = gw; t < ntp; t += nw) {
+            for_warp_tiles(&c->tick_comp[r], ntp, gw, nw, [&](uint32_t t) {
                 if (r == 0)
                     compact_pairs_wtile<true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
                                               covered);
                 else
                     compact_pairs_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
                                                covered);
-            }
+            });
             mark_work(c);
-            grid_sync(ws.bar, gen, status);
+            MST_SYNC_OR_ABORT();
             log_phase(c, PH_COMPACT, r);
             extract_pairs(ws, c, n_next, gtid, gstride);
             mark_work(c);
-            grid_sync(ws.bar, gen, status);
+            MST_SYNC_OR_ABORT();
             const uint32_t m_t = ld_volatile_u32(&c->tail_cnt[0]);
             if (gtid == 0 && r + 1 <= (uint32_t)kMaxRounds) {
                 c->stat_m[r + 1] = m_t;
                 c->stat_n[r + 1] = n_next;
             }
-            tail_rounds<kFT>(ws, c, n_next, m_t, r + 1, sm);
+            tail_rounds<kFT>(ws, c, n_next, m_t, r + 1, sm, spin_limit);
             mark_work(c);
-            grid_sync(ws.bar, gen, status);
+            MST_SYNC_OR_ABORT();
             log_phase(c, PH_TAIL, r + 1);
             // components left and rounds run, as CTA 0 recorded them
             n_cur = n_next - ld_volatile_u32(&c->tail_added);
@@ -1261,7 +1386,7 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             for (size_t v = gtid; v < n_next; v += gstride)
                 ws.parent[v] = (int32_t)v;
         const uint32_t ntc = (m_cur + kCompWTile - 1) / kCompWTile;
-        for (uint32_t t = gw; t < ntc; t += nw) {
+        for_warp_tiles(&c->tick_comp[r], ntc, gw, nw, [&](uint32_t t) {
             if (covered) {
                 if (r == 0)
                     compact_wtile<true, true>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w,
@@ -1274,9 +1399,9 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
             } else {
                 compact_wtile<false>(ws, c, t, r, m_cur, n_next, n, wt, src, dst, w);
             }
-        }
+        });
         mark_work(c);
-        grid_sync(ws.bar, gen, status);
+        MST_SYNC_OR_ABORT();
         log_phase(c, PH_COMPACT, r);
         const uint32_t m_next = ld_volatile_u32(&c->cnt_m[r]);
         if (gtid == 0 && r + 1 <= (uint32_t)kMaxRounds) {
@@ -1288,7 +1413,7 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         m_cur = covered ? m : m_next;
         if (m_live == 0)
             break;
-        if (r + 1 >= (uint32_t)kMaxRounds || (ld_volatile_u32(status) & ST_TIMEOUT)) {
+        if (r + 1 >= (uint32_t)kMaxRounds) {
             if (gtid == 0)
                 atomicOr(status, ST_INTERNAL);
             break;
@@ -1299,10 +1424,10 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
     const uint32_t nte = (words + 31u) >> 5;
     const uint32_t cap = n > 0 ? n - 1 : 0;
     emit_count(ws, words, nte, gw, nw);
-    grid_sync(ws.bar, gen, status);
+    MST_SYNC_OR_ABORT();
     emit_range<kFT>(ws, c, nte, words, cap, out, sm);
     mark_work(c);
-    grid_sync(ws.bar, gen, status);
+    MST_SYNC_OR_ABORT();
     log_phase(c, PH_EMIT, r);
     if (gtid == 0) {
         finish(c, out_count, nte ? ld_volatile_u32(&c->emitted) : 0u, n, n_cur);
@@ -1311,6 +1436,8 @@ k_solve(Ws ws, const int32_t *src, const int32_t *dst, const uint32_t *w, int32_
         c->m_cur = 0;
     }
 }
+
+#undef MST_SYNC_OR_ABORT
 
 // ------------------------------------------------ kernels of the graph path
 
@@ -1537,10 +1664,12 @@ void single_release(Single &s)
     if (s.base)
         cudaFree(s.base);
     const int schedule = s.schedule, bps = s.fused_blocks_per_sm, ft = s.fused_threads;
+    const uint32_t wait_limit = s.wait_limit;
     s = Single();
     s.schedule = schedule;
     s.fused_blocks_per_sm = bps;
     s.fused_threads = ft;
+    s.wait_limit = wait_limit;
 }
 
 #define MST_TRY(x)                     \
@@ -1731,6 +1860,42 @@ static cudaError_t begin_solve(Single &s, cudaStream_t stream)
     return cudaMemsetAsync(from, 0, (size_t)(to - from), stream);
 }
 
+// Fused solves on one device are ordered among themselves.  A fused grid
+// waits on itself at grid barriers, so all its CTAs must be resident at
+// once; two fused grids launched at the same time (other streams, other
+// handles, the server's lane) could each be left partly resident and wait
+// until their barriers give up.  So every fused launch on a device first
+// waits (on its own stream) for the previous fused launch on that device
+// to finish, through one event per device recorded after each launch.  The
+// chain holds across handles and streams of the process; other kernels
+// (batched solves, copies) still run beside a fused solve.  A stream that
+// is being captured into a CUDA graph is left out of the chain: the caller
+// orders what it replays.
+struct FusedChain {
+    std::mutex mu;
+    cudaEvent_t last = nullptr;
+};
+static FusedChain g_fused_chain[64];
+
+template <typename F>
+static cudaError_t ordered_fused_launch(cudaStream_t stream, F &&launch)
+{
+    int dev = 0;
+    MST_TRY(cudaGetDevice(&dev));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MST_TRY(cudaStreamIsCapturing(stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone || dev < 0 || dev >= 64)
+        return launch();
+    FusedChain &ch = g_fused_chain[dev];
+    std::lock_guard<std::mutex> lk(ch.mu);
+    if (!ch.last)
+        MST_TRY(cudaEventCreateWithFlags(&ch.last, cudaEventDisableTiming));
+    else
+        MST_TRY(cudaStreamWaitEvent(stream, ch.last, 0));
+    MST_TRY(launch());
+    return cudaEventRecord(ch.last, stream);
+}
+
 cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, const void *w,
                           uint32_t wt, int32_t *out, int64_t *out_count, uint32_t n, uint32_t m,
                           cudaStream_t stream, int grid, const InputCopy *copy)
@@ -1752,9 +1917,12 @@ cudaError_t single_launch(Single &s, const int32_t *src, const int32_t *dst, con
         uint32_t *cw = copy ? (uint32_t *)copy->w : nullptr;
         void *args[] = {(void *)&s.ws, (void *)&src, (void *)&dst, (void *)&wp, (void *)&out,
                         (void *)&out_count, (void *)&n, (void *)&m, (void *)&wt, (void *)&vec,
-                        (void *)&csrc, (void *)&cdst, (void *)&cw, (void *)&variant};
-        return cudaLaunchCooperativeKernel(fused_kernel(threads), dim3(g), dim3(threads), args,
-                                           0, stream);
+                        (void *)&csrc, (void *)&cdst, (void *)&cw, (void *)&variant,
+                        (void *)&s.wait_limit};
+        return ordered_fused_launch(stream, [&] {
+            return cudaLaunchCooperativeKernel(fused_kernel(threads), dim3(g), dim3(threads),
+                                               args, 0, stream);
+        });
     }
     if (!s.exec)
         MST_TRY(build_graph(s));
@@ -1914,7 +2082,7 @@ cudaError_t single_phase_profile(Single &s, cudaStream_t stream, std::vector<Ker
         }
         std::string name = std::string("k_solve:") + names[k];
         if (k == PH_HOOK || k == PH_COMPRESS || k == PH_COMPACT || k == PH_ROOTS)
-            name += r == 0 ? "@r0" : "@r1+";
+            name += r < 3 ? "@r" + std::to_string(r) : std::string("@r3+");
         add(name, ms, b);
         if (c.work_ns[i] > c.phase_ns[i - 1] && c.work_ns[i] <= c.phase_ns[i]) {
             wait_ms += (double)(c.phase_ns[i] - c.work_ns[i]) * 1e-6;

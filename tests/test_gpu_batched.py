@@ -165,3 +165,51 @@ def test_config4_full_batch_sampled(handle):
     status, cnt = run_batch(handle, b, sample=300, seed=4)
     assert status == B.MST_OK
     assert np.array_equal(cnt, np.diff(b.vtx_off) - 1)  # every graph is connected
+
+
+def test_batch_per_graph_status(handle):
+    """A NaN weight or an out-of-range vertex id in one graph, and a forest in
+    another, are reported for those graphs only: their batch-mates return
+    MST_OK and the oracle's trees, and the combined status is the union."""
+    b = gg.batched(40, 64, 4000, 6, 4242, weights="f32")
+    nan_g, bad_g, forest_g = 3, 17, 29
+    w = b.w.copy()
+    w[b.edge_off[nan_g] + 5] = np.float32("nan")
+    src = b.src.copy()
+    src[b.edge_off[bad_g] + 2] = int(b.vtx_off[bad_g + 1] - b.vtx_off[bad_g]) + 3
+    # graph forest_g: every edge end at its last vertex moves to vertex 0 (or
+    # 1, never making a self-loop), which leaves that vertex isolated and the
+    # graph a forest of two trees
+    e0, e1 = int(b.edge_off[forest_g]), int(b.edge_off[forest_g + 1])
+    n_f = int(b.vtx_off[forest_g + 1] - b.vtx_off[forest_g])
+    dst = b.dst.copy()
+    iso = n_f - 1
+    for e in range(e0, e1):
+        if src[e] == iso:
+            src[e] = 0 if dst[e] != 0 else 1
+        if dst[e] == iso:
+            dst[e] = 0 if src[e] != 0 else 1
+    b2 = gg.Batch(b.vtx_off, b.edge_off, src, dst, w, "per-graph status")
+    vo, eo, s, d, ww = to_dev(b2.vtx_off, b2.edge_off, b2.src, b2.dst, b2.w)
+    tn, tm = int(b2.vtx_off[-1]), int(b2.edge_off[-1])
+    out = torch.full((tn,), -9, dtype=torch.int32, device="cuda")
+    cnt = torch.full((b2.G,), -9, dtype=torch.int64, device="cuda")
+    assert B.mst_solve_batched(handle, B.MST_W_F32, b2.G, vo, eo, tn, tm, s, d, ww, out,
+                               cnt) == B.MST_OK
+    assert B.mst_get_status(handle) == B.MST_ERR_INVALID_ARG  # the union of all graphs
+    st, per = B.mst_get_batched_status(handle, b2.G)
+    assert st == B.MST_OK
+    out_h, cnt_h = out.cpu().numpy(), cnt.cpu().numpy()
+    for g in range(b2.G):
+        if g in (nan_g, bad_g):
+            assert per[g] == B.MST_ERR_INVALID_ARG, (g, per[g])
+            continue
+        gr = b2.graph(g)
+        assert per[g] == (B.MST_ERR_DISCONNECTED if g == forest_g else B.MST_OK), (g, per[g])
+        got = out_h[b2.vtx_off[g]: b2.vtx_off[g] + cnt_h[g]].astype(np.int64)
+        assert np.array_equal(got, oracle.kruskal(gr.n, gr.src, gr.dst, gr.w)), g
+    # after a single-graph solve there is no batch to report on
+    g0 = b2.graph(0)
+    s0, d0, w0 = to_dev(g0.src, g0.dst, g0.w)
+    B.solve(handle, g0.n, s0, d0, w0)
+    assert B.mst_get_batched_status(handle, b2.G)[0] == B.MST_ERR_INVALID_ARG

@@ -135,7 +135,50 @@ def test_serving_large_requests_use_fused_path(lib_built):
         assert B.mst_server_drain(h) == B.MST_OK
         for t, g, out, cnt, _ in reqs:
             st, lat = res[t]
-            assert st == B.MST_OK and lat > 0, g.name
+            # a forest reports what mst_solve_ex reports for it alone
+            want = B.MST_ERR_DISCONNECTED if g is forest else B.MST_OK
+            assert st == want and lat > 0, (g.name, B.mst_status_string(st))
+            got = out[: int(cnt.item())].cpu().numpy().astype(np.int64)
+            assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w)), g.name
+    finally:
+        B.mst_server_stop(h)
+        B.mst_destroy(h)
+
+
+def test_serving_bad_request_does_not_poison_its_batch(lib_built):
+    """Requests batched together each get their own status: one with a NaN
+    weight and one with an out-of-range vertex id report MST_ERR_INVALID_ARG,
+    a forest reports MST_ERR_DISCONNECTED, and every other request of the
+    same batches returns MST_OK with the oracle's tree."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    graphs = [gg.random_connected(800 + 97 * i, 2400 + 300 * i, 300 + i, weights="f32")
+              for i in range(24)]
+    nan = graphs[5]
+    nan.w = nan.w.copy()
+    nan.w[7] = np.float32("nan")
+    badv = graphs[11]
+    badv.src = badv.src.copy()
+    badv.src[3] = badv.n + 1
+    a = gg.random_connected(900, 2700, 350, weights="f32")
+    b = gg.random_connected(600, 1800, 351, weights="f32")
+    forest = gg.Graph(a.n + b.n, np.r_[a.src, b.src + a.n].astype(np.int32),
+                      np.r_[a.dst, b.dst + a.n].astype(np.int32), np.r_[a.w, b.w], "forest")
+    graphs[17] = forest
+    h = B.mst_create(0, 0)
+    try:
+        # one stream and a large max_batch: the requests share batches
+        assert B.mst_server_start(h, 1, 64) == B.MST_OK
+        reqs = submit_all(h, graphs)
+        res = wait_all(h, reqs)
+        assert B.mst_server_drain(h) == B.MST_OK
+        for t, g, out, cnt, _ in reqs:
+            st, _ = res[t]
+            if g is nan or g is badv:
+                assert st == B.MST_ERR_INVALID_ARG, B.mst_status_string(st)
+                continue
+            want = B.MST_ERR_DISCONNECTED if g is forest else B.MST_OK
+            assert st == want, (g.name, B.mst_status_string(st))
             got = out[: int(cnt.item())].cpu().numpy().astype(np.int64)
             assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w)), g.name
     finally:

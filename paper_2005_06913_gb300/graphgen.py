@@ -257,19 +257,35 @@ def _log_uniform_sizes(rng, count, lo, hi):
     return np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), count))).astype(np.int64)
 
 
+def _one_graph(args):
+    n, m, seed, weights = args
+    return random_connected(n, m, seed, weights=weights)
+
+
 def batched(G: int, nmin: int, nmax: int, degree: int, seed: int,
-            weights: str = "u32") -> Batch:
+            weights: str = "u32", workers: int = 1) -> Batch:
     """G independent ``random_connected`` graphs, vertex counts log-uniform in
     [nmin, nmax], m_g = n_g*degree/2, each with its own sub-seed; packed with
-    int64 ``vtx_off``/``edge_off`` offset tables (graph-local ids)."""
+    int64 ``vtx_off``/``edge_off`` offset tables (graph-local ids).  With
+    ``workers`` > 1 the graphs are made by that many processes (started with
+    ``spawn``); every graph depends only on its sub-seed, so the batch is the
+    same either way."""
     rng = np.random.default_rng(seed)
     ns = _log_uniform_sizes(rng, G, nmin, nmax)
     subseeds = rng.integers(0, 2 ** 63 - 1, G)
-    parts = []
+    jobs = []
     for g in range(G):
         n = int(ns[g])
         m = min(n * degree // 2, n * (n - 1) // 2)
-        parts.append(random_connected(n, m, int(subseeds[g]), weights=weights))
+        jobs.append((n, m, int(subseeds[g]), weights))
+    if workers > 1 and G > 1:
+        import multiprocessing
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers,
+                                 mp_context=multiprocessing.get_context("spawn")) as ex:
+            parts = list(ex.map(_one_graph, jobs, chunksize=max(1, G // (8 * workers))))
+    else:
+        parts = [_one_graph(j) for j in jobs]
     vtx_off = np.zeros(G + 1, np.int64)
     edge_off = np.zeros(G + 1, np.int64)
     vtx_off[1:] = np.cumsum([p.n for p in parts])
@@ -323,10 +339,11 @@ def csr_entries(c: CSR) -> Graph:
     return Graph(c.n, rows, c.col.copy(), c.w.copy(), "csr-entries")
 
 
-def serving_pool(P: int, nmin: int, nmax: int, degree: int, seed: int) -> Batch:
+def serving_pool(P: int, nmin: int, nmax: int, degree: int, seed: int,
+                 workers: int = 1) -> Batch:
     """A pool of P graphs for the serving benchmark: log-uniform vertex counts
     in [nmin, nmax], average degree ``degree``, float32 weights in (0,1)."""
-    return batched(P, nmin, nmax, degree, seed, weights="f32")
+    return batched(P, nmin, nmax, degree, seed, weights="f32", workers=workers)
 
 
 def paper_table1(name: str, seed: int = SEED_BASE) -> Graph:

@@ -287,8 +287,9 @@ mst_status mst_set_batched_schedule(mst_handle h, int schedule, int block_thread
 
 /*
  * Autotunes the batched solver on the given batch (same arguments as
- * mst_solve_batched): times each candidate schedule once per size bucket,
- * keeps the fastest, and, when cache_path is not NULL, stores the choice as
+ * mst_solve_batched): times each candidate schedule five times (after one
+ * warm-up launch) per size bucket, keeps the one with the lowest median,
+ * and, when cache_path is not NULL, stores the choice as
  * JSON there (and loads it on later calls).  Synchronises `stream`.
  */
 mst_status mst_autotune_batched(mst_handle h, mst_weight_type wt, int32_t G,

@@ -1157,6 +1157,8 @@ uint32_t batched_status_bits(Batched &b, cudaStream_t stream, cudaError_t *err)
     return bits;
 }
 
+constexpr int kTuneRuns = 5;  // timed launches per autotune candidate (median)
+
 cudaError_t batched_autotune(Batched &b, int device, uint32_t wt, int32_t G,
                              const int64_t *vtx_off, const int64_t *edge_off, uint64_t total_n,
                              uint64_t total_m, const int32_t *src, const int32_t *dst,
@@ -1188,12 +1190,17 @@ cudaError_t batched_autotune(Batched &b, int device, uint32_t wt, int32_t G,
             cudaGetLastError();
             continue;
         }
-        MST_TRY(cudaEventRecord(e0, stream));
-        MST_TRY(run_batched(b, device, ws, job, c, stream));
-        MST_TRY(cudaEventRecord(e1, stream));
-        MST_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        MST_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        // the median of kTuneRuns timed launches decides, not one sample
+        float runs[kTuneRuns];
+        for (int k = 0; k < kTuneRuns; k++) {
+            MST_TRY(cudaEventRecord(e0, stream));
+            MST_TRY(run_batched(b, device, ws, job, c, stream));
+            MST_TRY(cudaEventRecord(e1, stream));
+            MST_TRY(cudaEventSynchronize(e1));
+            MST_TRY(cudaEventElapsedTime(&runs[k], e0, e1));
+        }
+        std::sort(runs, runs + kTuneRuns);
+        const float ms = runs[kTuneRuns / 2];
         if (ms < best) {
             best = ms;
             bestc = c;

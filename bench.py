@@ -26,6 +26,7 @@ workload, rank 0 only.
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import os
 import statistics
@@ -507,19 +508,23 @@ def _percentiles(xs):
     return pick(0.50), pick(0.99)
 
 
-def batched_measure(B, h, stream, b, steps, warmup, per_graph_sample, sample_oracle=0):
+def batched_measure(B, h, stream, b, steps, warmup, per_graph_sample, sample_oracle=0,
+                    autotune=True):
     """Times `steps` mst_solve_batched launches of batch b (inputs resident;
-    the autotuner picks the schedule first) and, on a sample of its graphs,
-    the same graphs one launch per graph.  Returns the block's fields."""
+    the autotuner picks the schedule first, unless autotune is False) and, on
+    a sample of its graphs, the same graphs one launch per graph.  Returns
+    the block's fields."""
     import torch
     tn, tm = int(b.vtx_off[-1]), int(b.edge_off[-1])
     dev = lambda a: torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).cuda()
     vo, eo, s, d, w = dev(b.vtx_off), dev(b.edge_off), dev(b.src), dev(b.dst), dev(b.w)
     out = torch.empty(max(tn, 1), dtype=torch.int32, device="cuda")
     cnt = torch.zeros(max(b.G, 1), dtype=torch.int64, device="cuda")
-    st = B.mst_autotune_batched(h, B.MST_W_U32, b.G, vo, eo, tn, tm, s, d, w, out, cnt, None, stream)
-    if st != B.MST_OK:
-        raise B.MstError(st, "autotune")
+    if autotune:
+        st = B.mst_autotune_batched(h, B.MST_W_U32, b.G, vo, eo, tn, tm, s, d, w, out, cnt, None,
+                                    stream)
+        if st != B.MST_OK:
+            raise B.MstError(st, "autotune")
 
     def solve_batch():
         st = B.mst_solve_batched(h, B.MST_W_U32, b.G, vo, eo, tn, tm, s, d, w, out, cnt, stream)
@@ -667,7 +672,8 @@ def run_batched(args):
     if dist is not None:
         dist.barrier()
     blk = batched_measure(B, h, stream, b, args.steps, args.warmup,
-                          args.per_graph_sample if rank == 0 and ws == 1 else 0)
+                          args.per_graph_sample if rank == 0 and ws == 1 else 0,
+                          autotune=not args.no_autotune)
     clk.mark(*blk.pop("window"))
     clk.stop()
     total_ms = blk.pop("total_ms")
@@ -764,7 +770,10 @@ def run_serving(args):
                 tickets[t] = slot
                 slot_busy[slot] = t
                 k += 1
-            for t in list(tickets):
+            # poll the oldest outstanding requests (completion is nearly in
+            # arrival order; the server stamps each latency itself, so a late
+            # poll does not lengthen it)
+            for t in list(itertools.islice(tickets, 256)):
                 st, dn, l_us = B.mst_poll(h, t)
                 if dn:
                     errors += int(st != B.MST_OK)
@@ -920,6 +929,8 @@ def main():
                     default="single")
     ap.add_argument("--graphs", type=int, default=4096)
     ap.add_argument("--per-graph-sample", type=int, default=256)
+    # the batch's built-in schedule instead of the autotuner's (profiling)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pool", type=int, default=1024)
     ap.add_argument("--serve-nmax", type=int, default=1048576)
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000")

@@ -714,7 +714,9 @@ def run_serving(args):
     device-memory budget.  Reports graphs/s completed and p50/p99 request
     latency per rate, the saturation knee, and the same arrival streams
     served one solve at a time (single-graph kernel, one stream) for
-    comparison."""
+    comparison.  A request's latency is its completion minus its arrival
+    (the server's own completion-minus-submit, plus any time the request
+    was held back because the output ring was full)."""
     import torch
 
     from paper_2005_06913_gb300 import binding as B
@@ -757,8 +759,17 @@ def run_serving(args):
         errors = 0
         t_start = time.perf_counter()
         k = 0
+        # an overloaded stream is cut off at 1.2x its span: arrivals not yet
+        # submitted then are counted as unserved (with their wait so far as a
+        # lower bound on their latency), and requests in flight are drained
+        cut = 1.2 * args.seconds
+        unserved = 0
         while k < arrivals.shape[0] or tickets:
             now = time.perf_counter() - t_start
+            if now > cut and k < arrivals.shape[0]:
+                unserved = int(arrivals.shape[0] - k)
+                lat.extend((now - arrivals[k:]) * 1e3)
+                k = arrivals.shape[0]
             while k < arrivals.shape[0] and arrivals[k] <= now:
                 slot = k % ring
                 if slot in slot_busy:  # ring full: the stream is overloaded, wait
@@ -767,7 +778,9 @@ def run_serving(args):
                 e0 = int(g_e0[g])
                 st, t = B.mst_submit(h, B.MST_W_F32, int(g_n[g]), int(g_m[g]), ps + 4 * e0,
                                      pd + 4 * e0, pw + 4 * e0, po + 4 * nmax * slot, pc + 8 * slot)
-                tickets[t] = slot
+                # a request held back while the output ring was full waited
+                # from its arrival, not from its submission
+                tickets[t] = (slot, now - arrivals[k])
                 slot_busy[slot] = t
                 k += 1
             # poll the oldest outstanding requests (completion is nearly in
@@ -777,16 +790,18 @@ def run_serving(args):
                 st, dn, l_us = B.mst_poll(h, t)
                 if dn:
                     errors += int(st != B.MST_OK)
-                    slot_busy.pop(tickets.pop(t), None)
-                    lat.append(l_us * 1e-3)
+                    slot, held = tickets.pop(t)
+                    slot_busy.pop(slot, None)
+                    lat.append(l_us * 1e-3 + max(held, 0.0) * 1e3)
                     done_t.append(time.perf_counter() - t_start)
             time.sleep(0.0002)
         elapsed = max(done_t) if done_t else 1.0
         B.mst_server_stop(h)
         B.mst_destroy(h)
         p50, p99 = _percentiles(lat)
-        results.append({"rate_offered": rate, "requests": len(lat), "errors": errors,
-                        "graphs_per_s": len(lat) / elapsed, "latency_ms": {"p50": p50, "p99": p99}})
+        results.append({"rate_offered": rate, "requests": int(arrivals.shape[0]),
+                        "completed": len(done_t), "unserved_at_cut": unserved, "errors": errors,
+                        "graphs_per_s": len(done_t) / elapsed, "latency_ms": {"p50": p50, "p99": p99}})
     # the same arrival streams served one solve at a time (single-graph
     # kernel, one stream, FIFO): what the same kernels give without batching.
     # A stream this arm cannot keep up with is cut off after 1.2x its span;

@@ -269,7 +269,22 @@ struct GraphArrays {
     unsigned long long *mA, *mB;
     int32_t *parent, *nid, *lab;
     uint32_t *bits;
+    // the pair table of the merging tail (shared memory left over by the
+    // graph's own arrays): once a round leaves at most tail_n components,
+    // parallel edges are merged (0: never)
+    unsigned long long *ptab = nullptr;
+    uint32_t tail_n = 0;
 };
+
+// Slot of component pair (a, b), a < b < n, in a triangular table.
+__device__ __forceinline__ uint32_t tri_slot(uint32_t a, uint32_t b, uint32_t n)
+{
+    return a * (2 * n - a - 1) / 2 + (b - a - 1);
+}
+
+__host__ __device__ __forceinline__ uint32_t tri_size(uint32_t n) { return n * (n - 1) / 2; }
+
+constexpr uint32_t kBTailMaxN = 128;  // components at which a graph's tail may start
 
 // Offers a key to a running minimum that may live in shared or global
 // memory (generic pointer): a filtered min (values only decrease, so a key
@@ -421,6 +436,178 @@ template <int T>
 __device__ __forceinline__ uint32_t get_total(const BlockTeam<T> &tm, uint32_t) { return *(volatile uint32_t *)tm.total; }
 __device__ __forceinline__ uint32_t get_total(const WarpTeam &, uint32_t run) { return run; }
 
+
+// ------------------------------------------------------- the merging tail
+//
+// Once a round leaves at most A.tail_n components, a block team stops
+// carrying every live edge from round to round.  Of the parallel edges
+// between two components only the lightest can be in the tree (a heavier one
+// closes a cycle with it), so the round's compaction keeps one record per
+// component pair in a triangular table in shared memory, and the remaining
+// Boruvka rounds run on those records: hook by edge (a record whose key is
+// the minimum of an endpoint hooks that endpoint), roots numbered, records
+// relabelled and merged again.  Records carry (a, b, weight bits, input id)
+// and keys are (weight, input id), so the order is the same as before.
+
+// Gathers the non-empty slots of the pair table into E (any order: keys
+// name their edges); returns their number.  After a team sync.
+template <int T>
+__device__ __forceinline__ uint32_t pairs_to_list(const BlockTeam<T> &tm, const GraphArrays &A,
+                                                  uint32_t n2)
+{
+    volatile uint32_t *cnt = tm.total;
+    if (threadIdx.x == 0)
+        *cnt = 0u;
+    tm.sync();
+    for (uint32_t i = threadIdx.x; i < n2 * n2; i += T) {
+        const uint32_t a = i / n2, b = i % n2;
+        if (a >= b)
+            continue;
+        const unsigned long long key = A.ptab[tri_slot(a, b, n2)];
+        if (key == kNoEdge)
+            continue;
+        const uint32_t pos = atomicAdd((uint32_t *)cnt, 1u);
+        A.E[pos] = make_uint4(a, b, (uint32_t)(key >> 32), (uint32_t)key);
+    }
+    tm.sync();
+    const uint32_t m2 = *cnt;
+    tm.sync();  // every thread has read the count before it is reused
+    return m2;
+}
+
+// The tail rounds on the m_t records of E among n_t components; returns the
+// components left.
+template <int T>
+__device__ uint32_t merge_tail(const BlockTeam<T> &tm, const GraphArrays &A, uint32_t n_t,
+                               uint32_t m_t, uint32_t *status)
+{
+    volatile uint32_t *cnt = tm.total;
+    volatile unsigned long long *tmin = A.mA;
+    volatile int32_t *par = A.parent;
+    volatile int32_t *nid = A.nid, *lab = A.lab;
+    const uint32_t t = threadIdx.x;
+    for (uint32_t tr = 0; m_t > 0; tr++) {
+        if (tr >= (uint32_t)kMaxRounds) {
+            if (t == 0)
+                atomicOr(status, ST_INTERNAL);
+            break;
+        }
+        for (uint32_t v = t; v < n_t; v += T) {
+            tmin[v] = kNoEdge;
+            par[v] = (int32_t)v;
+        }
+        tm.sync();
+        // find-min (Section 2.1, the loop over edges)
+        for (uint32_t e = t; e < m_t; e += T) {
+            const uint4 q = A.E[e];
+            const unsigned long long key = make_key(q.z, q.w);
+            offer_any((unsigned long long *)&tmin[q.x], key);
+            offer_any((unsigned long long *)&tmin[q.y], key);
+        }
+        tm.sync();
+        // hook by edge (Section 2.1, the union step); a mutual pair keeps the lower id
+        for (uint32_t e = t; e < m_t; e += T) {
+            const uint4 q = A.E[e];
+            const unsigned long long key = make_key(q.z, q.w);
+            const bool ha = tmin[q.x] == key, hb = tmin[q.y] == key;
+            if (ha && hb)
+                par[q.x > q.y ? q.x : q.y] = (int32_t)(q.x < q.y ? q.x : q.y);
+            else if (ha)
+                par[q.x] = (int32_t)q.y;
+            else if (hb)
+                par[q.y] = (int32_t)q.x;
+            if (ha || hb)
+                atomicOr(&A.bits[q.w >> 5], 1u << (q.w & 31));
+        }
+        if (t == 0)
+            *cnt = 0u;
+        tm.sync();
+        for (uint32_t v = t; v < n_t; v += T)  // roots take new ids
+            if ((uint32_t)par[v] == v)
+                nid[v] = (int32_t)atomicAdd((uint32_t *)cnt, 1u);
+        tm.sync();
+        const uint32_t n2 = *cnt;
+        for (uint32_t v = t; v < n_t; v += T) {  // a forest: depth < n_t
+            uint32_t x = v;
+            for (uint32_t hop = 0; hop < n_t; hop++) {
+                const uint32_t p = (uint32_t)par[x];
+                if (p == x)
+                    break;
+                x = p;
+            }
+            lab[v] = nid[x];
+        }
+        for (uint32_t i = t; i < tri_size(n2); i += T)
+            A.ptab[i] = kNoEdge;
+        tm.sync();
+        // merge: relabel, keep the lightest record per pair
+        for (uint32_t e = t; e < m_t; e += T) {
+            const uint4 q = A.E[e];
+            const uint32_t a = (uint32_t)lab[q.x], b = (uint32_t)lab[q.y];
+            if (a == b)
+                continue;
+            offer_any(&A.ptab[tri_slot(a < b ? a : b, a < b ? b : a, n2)], make_key(q.z, q.w));
+        }
+        tm.sync();
+        m_t = pairs_to_list(tm, A, n2);
+        n_t = n2;
+    }
+    return n_t;
+}
+
+// Entry into the merging tail from round r, after its compress: when the
+// round leaves 2..A.tail_n components, its compaction keeps the lightest
+// record per component pair instead of every edge, and the tail finishes
+// the graph.  Returns false (nothing done) otherwise; a warp team never
+// merges (its graphs are small).
+template <int T>
+__device__ bool merge_entry(const BlockTeam<T> &tm, const GraphArrays &A, uint32_t r, uint32_t n,
+                            uint32_t m_r, uint32_t n_next, const int32_t *src, const int32_t *dst,
+                            const uint32_t *w, uint32_t wt, uint32_t *status, uint32_t *n_left)
+{
+    if (!A.ptab || n_next < 2 || n_next > A.tail_n || m_r == 0)
+        return false;
+    for (uint32_t i = threadIdx.x; i < tri_size(n_next); i += T)
+        A.ptab[i] = kNoEdge;
+    tm.sync();
+    for (uint32_t i = threadIdx.x; i < m_r; i += T) {
+        uint32_t u, v, wb, id;
+        if (r == 0) {
+            u = (uint32_t)__ldg(src + i);
+            v = (uint32_t)__ldg(dst + i);
+            if (u >= n || v >= n || u == v)
+                continue;
+            wb = weight_bits(__ldg(w + i), wt, status);
+            id = i;
+        } else {
+            const uint4 q = A.E[i];
+            u = q.x;
+            v = q.y;
+            wb = q.z;
+            id = q.w;
+        }
+        const uint32_t a = (uint32_t)((volatile int32_t *)A.lab)[u];
+        const uint32_t b = (uint32_t)((volatile int32_t *)A.lab)[v];
+        if (a >= n_next || b >= n_next) {
+            atomicOr(status, ST_INTERNAL);
+            continue;
+        }
+        if (a != b)
+            offer_any(&A.ptab[tri_slot(a < b ? a : b, a < b ? b : a, n_next)], make_key(wb, id));
+    }
+    tm.sync();
+    const uint32_t m_t = pairs_to_list(tm, A, n_next);
+    *n_left = merge_tail(tm, A, n_next, m_t, status);
+    return true;
+}
+
+__device__ __forceinline__ bool merge_entry(const WarpTeam &, const GraphArrays &, uint32_t,
+                                            uint32_t, uint32_t, uint32_t, const int32_t *,
+                                            const int32_t *, const uint32_t *, uint32_t,
+                                            uint32_t *, uint32_t *)
+{
+    return false;
+}
 
 // All Boruvka rounds of one graph by one team.  Inputs are the graph's slice
 // of the caller's arrays (local ids); A the graph's working arrays.
@@ -575,6 +762,13 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
             }
         }
         tm.sync();
+        {
+            uint32_t n_left = 0;
+            if (merge_entry(tm, A, r, n, m_r, n_next, src, dst, w, wt, status, &n_left)) {
+                n_r = n_left;  // the tail finished the graph
+                break;
+            }
+        }
         // compact in place + find-min of the next round, warp tiles: a tile's
         // survivors move only to positions of tiles whose loads are done
         // (their aggregates were published after their loads)
@@ -738,6 +932,16 @@ __device__ __forceinline__ GraphArrays place(const BWs &ws, char *sm, size_t bud
         A.lab = ws.lab + vo;
         A.bits = ws.bits + (eo >> 5) + (uint64_t)g;
         A.E = ws.E + eo;
+    }
+    // the merging tail's pair table takes the shared memory left over
+    const size_t used = vb > budget ? 0 : (vb + eb <= budget ? vb + eb : vb);
+    const size_t left = budget - used;
+    uint32_t tn = kBTailMaxN;
+    while (tn >= 8 && (size_t)tri_size(tn) * 8 > left)
+        tn--;
+    if (tn >= 8) {
+        A.ptab = (unsigned long long *)(sm + used);
+        A.tail_n = tn;
     }
     return A;
 }

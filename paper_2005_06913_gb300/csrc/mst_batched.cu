@@ -289,14 +289,17 @@ constexpr uint32_t kBTailMaxN = 128;  // components at which a graph's tail may 
 // Offers a key to a running minimum that may live in shared or global
 // memory (generic pointer): a filtered min (values only decrease, so a key
 // not below the current value cannot win), as a fire-and-forget reduction
-// in global memory and an atomic in shared memory.
+// in global memory and an atomic in shared memory.  In global memory the
+// filter reads through L1: an older value only lets a key through, and the
+// phases that use the minima read them after the team's barrier (measured:
+// the 4,096-graph batch 3% faster than with volatile filter loads).
 __device__ __forceinline__ void offer_any(unsigned long long *p, unsigned long long key)
 {
-    if (key < *(volatile unsigned long long *)p) {
-        if (__isGlobal(p))
+    if (__isGlobal(p)) {
+        if (key < __ldca(p))
             red_min_u64(p, key);  // fire-and-forget in L2
-        else
-            atomicMin(p, key);
+    } else if (key < *(volatile unsigned long long *)p) {
+        atomicMin(p, key);
     }
 }
 

@@ -846,6 +846,12 @@ __device__ __forceinline__ void finish(Ctl *c, int64_t *out_count, uint32_t emit
 // bit flips exactly when the last block arrives and its low bits return to
 // where they were; each block spins until the top bit differs from the
 // value it saw when it arrived.  One atomic per block, nothing to reset.
+// Thread 0 arrives with a gpu-scope release atomic and polls with
+// gpu-scope acquire loads; the block barriers before and after make the
+// pattern cover every thread of the CTA (the PTX model's release is
+// cumulative over what bar.sync ordered before it).  Measured against full
+// fences around a relaxed atomic: grid 1024^2 0.340 -> 0.323 ms, random
+// 4,096 / 32,768 0.116 -> 0.109 ms.
 // Waits are bounded (spin_limit polls; 0 means kBarSpinLimit): on expiry
 // ST_TIMEOUT is set, later barriers no longer wait, and the barrier tells
 // every thread of the CTA to abandon the solve.
@@ -865,23 +871,29 @@ __device__ __forceinline__ bool team_sync(uint32_t *counter, uint32_t nb, uint32
     if (threadIdx.x == 0) {
         const uint32_t limit = spin_limit ? spin_limit : kBarSpinLimit;
         const uint32_t inc = blockIdx.x == 0 ? 0x80000000u - (nb - 1) : 1u;
-        __threadfence();
-        const uint32_t old = atomicAdd(counter, inc);
+        uint32_t old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;"
+                     : "=r"(old)
+                     : "l"(counter), "r"(inc)
+                     : "memory");
         uint32_t spins = 0;
-        while (((old ^ ld_volatile_u32(counter)) & 0x80000000u) == 0) {
+        for (;;) {
+            uint32_t now;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(counter) : "memory");
+            if (((old ^ now) & 0x80000000u) != 0)
+                break;
             if (++spins > limit) {
                 atomicOr(status, ST_TIMEOUT);
                 if (!spin_limit)  // a real give-up, not an injected short limit
                     printf("mst: grid barrier gave up: block %u of %u, arrival value %u, now %u\n",
-                           blockIdx.x, nb, old, ld_volatile_u32(counter));
+                           blockIdx.x, nb, old, now);
                 break;
             }
-            if (ld_volatile_u32(status) & ST_TIMEOUT)
-                break;
+            if ((spins & 15) == 0 && (ld_volatile_u32(status) & ST_TIMEOUT))
+                break;  // another CTA gave up: stop waiting
             if (spins > 64)
                 __nanosleep(32);
         }
-        __threadfence();
         s_abort = (ld_volatile_u32(status) & ST_TIMEOUT) ? 1u : 0u;
     }
     __syncthreads();

@@ -213,3 +213,53 @@ def test_batch_per_graph_status(handle):
     s0, d0, w0 = to_dev(g0.src, g0.dst, g0.w)
     B.solve(handle, g0.n, s0, d0, w0)
     assert B.mst_get_batched_status(handle, b2.G)[0] == B.MST_ERR_INVALID_ARG
+
+
+def _multigraph(n, m, seed, weights):
+    """A connected multigraph: a random spanning tree plus m - (n - 1) edges
+    drawn among few vertex groups, so that after a round or two almost every
+    live edge is parallel to others between the same components; weights
+    with heavy ties."""
+    rng = np.random.default_rng(seed)
+    tv = np.arange(1, n)
+    tu = rng.integers(0, tv)
+    k = m - (n - 1)
+    groups = rng.integers(0, 6, n)
+    a = rng.integers(0, n, k)
+    b = rng.integers(0, n, k)
+    b = np.where(groups[a] == groups[b], (b + 1) % n, b)  # cross-group extra edges
+    src = np.r_[tv, a].astype(np.int32)
+    dst = np.r_[tu, b].astype(np.int32)
+    if weights == "f32":
+        w = (rng.integers(0, 16, m) / 16.0).astype(np.float32)
+    else:
+        w = rng.integers(0, 40, m).astype(np.uint32)
+    return gg.Graph(n, src, dst, w)
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512, 1024])
+@pytest.mark.parametrize("weights", ["u32", "f32"])
+def test_batch_merging_tail(handle, threads, weights):
+    """Graphs whose rounds reach few components while most live edges are
+    parallel: the block team's merging tail keeps the lightest record per
+    component pair, ties broken by edge id.  Also a forest with isolated
+    vertices and graphs in global and in shared memory."""
+    parts = [_multigraph(n, 6 * n, 600 + n, weights) for n in (300, 1500, 5000, 30000)]
+    a, c = _multigraph(2000, 9000, 701, weights), _multigraph(900, 4000, 702, weights)
+    parts.append(gg.Graph(2900 + 50, np.r_[a.src, c.src + 2000].astype(np.int32),
+                          np.r_[a.dst, c.dst + 2000].astype(np.int32), np.r_[a.w, c.w]))
+    vo = np.r_[0, np.cumsum([p.n for p in parts])].astype(np.int64)
+    eo = np.r_[0, np.cumsum([p.m for p in parts])].astype(np.int64)
+    wdt = np.float32 if weights == "f32" else np.uint32
+    b = gg.Batch(vo, eo, np.concatenate([p.src for p in parts]).astype(np.int32),
+                 np.concatenate([p.dst for p in parts]).astype(np.int32),
+                 np.concatenate([p.w for p in parts]).astype(wdt))
+    B.mst_set_batched_schedule(handle, 1, threads)
+    try:
+        status, cnt = run_batch(handle, b)
+    finally:
+        B.mst_set_batched_schedule(handle, 0, 0)
+    assert status == B.MST_ERR_DISCONNECTED  # the last graph is a forest
+    st, per = B.mst_get_batched_status(handle, b.G)
+    assert st == B.MST_OK and per[:-1] == [B.MST_OK] * (b.G - 1)
+    assert per[-1] == B.MST_ERR_DISCONNECTED and cnt[-1] == 2950 - 52

@@ -344,10 +344,13 @@ mst_status mst_solve_noalloc(mst_weight_type wt, int32_t n, int64_t m,
  * admits new requests as soon as a stream and memory are free, so solves of
  * requests that arrive while others run overlap on the GPU.  max_batch caps
  * the graphs per launch.  A request with more than 131072 edges is not
- * batched: it is solved alone by the fused single-graph kernel in a workspace
- * owned by its stream (on the whole co-resident grid when nothing else is in
- * flight, else on half of it), one such request at a time, while small
- * requests keep being batched past it on other streams.
+ * batched with the small ones: it goes to the fused lane, where the fused
+ * single-graph kernel solves it in a workspace owned by the server (on the
+ * whole co-resident grid when nothing else is in flight, else on half of
+ * it), while small requests keep being batched past it on other streams.
+ * Lane requests that queue up behind one another (up to 16, of one weight
+ * type) are solved in one launch as a single union graph and cut back
+ * apart, which gives each the tree and the status of a solve of it alone.
  */
 mst_status mst_server_start(mst_handle h, int streams, int max_batch);
 

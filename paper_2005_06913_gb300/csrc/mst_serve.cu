@@ -34,6 +34,16 @@ constexpr int64_t kServeBigM = 131072;  // larger requests always get the fused 
 constexpr int64_t kServeMidM = 16384;   // larger ones wait for it ...
 constexpr int kServeLaneDepth = 4;       // ... unless this many are ahead of them
 
+// One request of a fused-lane union (see k_lane_gather).
+struct LaneDesc {
+    const int32_t *src, *dst;
+    const uint32_t *w;
+    int32_t *out;
+    int64_t *out_count;
+    uint32_t n, m;
+    uint32_t vbase, ebase;  // the request's first vertex and edge in the union
+};
+
 struct Slot {
     bool big = false;             // the request in flight is a large one
     cudaStream_t stream = nullptr;
@@ -44,6 +54,8 @@ struct Slot {
     void *ws = nullptr;           // workspace of the batch in flight
     size_t ws_bytes = 0;
     uint64_t total_n = 0, total_m = 0;  // the batch's totals (locate per-graph status)
+    LaneDesc *h_lane = nullptr;   // pinned host descriptors of a lane union
+    int lane_k = 0;               // requests in the lane union in flight (0: one request)
     std::vector<uint64_t> tickets;
     bool busy = false;
 };
@@ -64,6 +76,8 @@ struct Server {
     std::unordered_map<uint64_t, double> submit_us;
     std::vector<Slot> slots;
     Single lane;  // fused-kernel workspace of the (single) large-request lane
+    void *ubuf = nullptr;  // the lane union's copies of its requests, descriptors, flags
+    size_t ubuf_bytes = 0;
     std::vector<std::pair<void *, size_t>> retired;  // outgrown lane workspaces, freed at
                                                      // stop (or when memory runs short)
     int max_batch = 256;
@@ -74,6 +88,111 @@ struct Server {
     bool stop = false;
     cudaError_t error = cudaSuccess;
 };
+
+// ------------------------------------------------------- the fused lane's unions
+//
+// Requests queued for the fused lane are solved together: their graphs are
+// copied side by side into one union graph (vertex ids shifted by the
+// request's vertex base, edge ids by its edge base), the fused kernel
+// solves the union once, and each request's ids are cut back out of the
+// union's ascending output.  The minimum spanning forest of a disjoint
+// union is the union of the graphs' own forests (no edge joins two
+// requests), and an edge's order (weight, id) within its request is the
+// same in the union, so each request gets exactly the tree it gets alone;
+// the union pays the fused kernel's per-round barriers once for all of them.
+
+constexpr int kLaneBatch = 16;            // requests per union at most
+constexpr int64_t kLaneMaxM = 1ll << 25;  // edges per union at most (unless one request alone)
+
+// Copies request blockIdx.y into the union.  An edge with an endpoint out of
+// range becomes a self-loop (the solve ignores both alike) and a NaN weight
+// is copied as is (it sorts after every other weight, alone or in the
+// union); either is recorded in the request's flag, so the request, and
+// only it, reports MST_ERR_INVALID_ARG.
+__global__ void k_lane_gather(const LaneDesc *d, uint32_t wt, int32_t *us, int32_t *ud,
+                              uint32_t *uw, uint32_t *flags)
+{
+    const LaneDesc q = d[blockIdx.y];
+    bool bad = false;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < q.m; i += gridDim.x * blockDim.x) {
+        uint32_t u = (uint32_t)__ldg(q.src + i), v = (uint32_t)__ldg(q.dst + i);
+        const uint32_t x = __ldg(q.w + i);
+        if (u >= q.n || v >= q.n) {
+            bad = true;
+            u = v = 0;
+        }
+        if (wt && (x & 0x7fffffffu) > 0x7f800000u)
+            bad = true;
+        us[q.ebase + i] = (int32_t)(q.vbase + u);
+        ud[q.ebase + i] = (int32_t)(q.vbase + v);
+        uw[q.ebase + i] = x;
+    }
+    if (__syncthreads_or(bad ? 1 : 0) && threadIdx.x == 0)
+        atomicOr(&flags[blockIdx.y], 1u);
+}
+
+// First position of ids[0..cnt) (ascending) that is >= x.
+__device__ __forceinline__ uint32_t lower_pos(const int32_t *ids, uint32_t cnt, uint32_t x)
+{
+    uint32_t lo = 0, hi = cnt;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint32_t)ids[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Cuts request blockIdx.x's ids out of the union's output and records its
+// status: MST_ERR_INVALID_ARG if flagged, MST_ERR_DISCONNECTED if its ids do
+// not span it, else MST_OK (a wait that ran out is reported from the
+// union's own status word, for every request of the union).
+__global__ void k_lane_scatter(const LaneDesc *d, const int32_t *uo, const int64_t *ucnt,
+                               const uint32_t *flags, int32_t *stat)
+{
+    __shared__ uint32_t s_lo, s_hi;
+    const LaneDesc q = d[blockIdx.x];
+    if (threadIdx.x == 0) {
+        const uint32_t total = (uint32_t)*ucnt;
+        s_lo = lower_pos(uo, total, q.ebase);
+        s_hi = lower_pos(uo, total, q.ebase + q.m);
+    }
+    __syncthreads();
+    const uint32_t lo = s_lo, k = s_hi - s_lo;
+    const uint32_t cap = q.n > 0 ? q.n - 1 : 0;
+    for (uint32_t i = threadIdx.x; i < k && i < cap; i += blockDim.x)
+        q.out[i] = uo[lo + i] - (int32_t)q.ebase;
+    if (threadIdx.x == 0) {
+        *q.out_count = (int64_t)(k < cap ? k : cap);
+        int32_t code = MST_OK;
+        if (flags[blockIdx.x])
+            code = MST_ERR_INVALID_ARG;
+        else if (k > cap)
+            code = MST_ERR_INTERNAL;
+        else if (q.n > 0 && k != cap)
+            code = MST_ERR_DISCONNECTED;
+        stat[blockIdx.x] = code;
+    }
+}
+
+// Layout of the lane union's buffer: descriptors, flags and statuses of up
+// to kLaneBatch requests, the union's count, copies of its edge arrays and
+// its output.
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+static size_t union_head()
+{
+    return al256(sizeof(LaneDesc) * kLaneBatch) + 2 * al256(4 * kLaneBatch) + al256(8);
+}
+static size_t union_bytes(uint64_t n_u, uint64_t m_u)
+{
+    return union_head() + 3 * al256(4 * m_u) + al256(4 * (n_u > 0 ? n_u : 1));
+}
+static int32_t *union_stat(void *base)
+{
+    return (int32_t *)((char *)base + al256(sizeof(LaneDesc) * kLaneBatch) + al256(4 * kLaneBatch));
+}
 
 // Workspace of one request inside a batch (edge list, vertex arrays, bits).
 static size_t request_bytes(uint32_t n, uint32_t m)
@@ -89,9 +208,15 @@ static void complete_slot(Server &S, Slot &sl)
     const double t = now_us();
     std::vector<uint32_t> bits(sl.tickets.size(), 0u);
     cudaError_t e = cudaSuccess;
+    std::vector<int32_t> lane_stat;
     if (sl.big) {
         e = cudaMemcpy(bits.data(), &S.lane.ws.ctl->status, sizeof(uint32_t),
                        cudaMemcpyDeviceToHost);
+        if (sl.lane_k > 0 && e == cudaSuccess) {  // a union: each request's own status
+            lane_stat.resize(sl.lane_k);
+            e = cudaMemcpy(lane_stat.data(), union_stat(S.ubuf), sl.lane_k * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost);
+        }
     } else {
         if (!bits.empty())
             e = desc_batch_graph_status(sl.ws, (int32_t)bits.size(), sl.total_n, sl.total_m,
@@ -104,7 +229,14 @@ static void complete_slot(Server &S, Slot &sl)
         Outcome &o = S.results[tk];
         o.done = true;
         o.latency_us = t - S.submit_us[tk];
-        o.status = e != cudaSuccess ? MST_ERR_CUDA : status_from_bits(bits[i]);
+        if (e != cudaSuccess)
+            o.status = MST_ERR_CUDA;
+        else if (!lane_stat.empty())  // a wait that ran out concerns the whole union
+            o.status = (bits[0] & (ST_TIMEOUT | ST_INTERNAL))
+                           ? status_from_bits(bits[0] & (ST_TIMEOUT | ST_INTERNAL))
+                           : (mst_status)lane_stat[i];
+        else
+            o.status = status_from_bits(bits[i]);
         S.submit_us.erase(tk);
     }
     if (!sl.big)
@@ -116,6 +248,7 @@ static void complete_slot(Server &S, Slot &sl)
     sl.ws = nullptr;
     sl.ws_bytes = 0;
     sl.big = false;
+    sl.lane_k = 0;
     sl.busy = false;
     S.cv.notify_all();
 }
@@ -170,8 +303,34 @@ static std::vector<Request> take_batch(Server &S, Slot &sl, size_t budget, bool 
                 continue;
             }
             batch.push_back(*it);
-            S.pending.erase(it);
+            it = S.pending.erase(it);
             *big = true;
+            // more requests of the same weight type join the union, in
+            // arrival order, while it stays within kLaneBatch requests,
+            // kLaneMaxM edges and the memory budget
+            int64_t n_u = batch[0].n, m_u = batch[0].m;
+            const size_t have_u = S.ubuf ? S.ubuf_bytes : 0;
+            for (auto jt = it; jt != S.pending.end() && (int)batch.size() < kLaneBatch;) {
+                if (jt->m <= kServeMidM || jt->wt != batch[0].wt || m_u + jt->m > kLaneMaxM ||
+                    n_u + jt->n > (int64_t)INT32_MAX) {
+                    ++jt;
+                    continue;
+                }
+                const int64_t n2 = n_u + jt->n, m2 = m_u + jt->m;
+                const size_t need2 = single_bytes((uint32_t)std::max<int64_t>(n2, 1024),
+                                                  (uint32_t)std::max<int64_t>(m2, 1024));
+                const size_t needu = union_bytes((uint64_t)n2, (uint64_t)m2);
+                const size_t grow =
+                    (need2 > have ? need2 - have : 0) + (needu > have_u ? needu - have_u : 0);
+                if (budget && S.in_use + grow > budget) {
+                    ++jt;
+                    continue;
+                }
+                batch.push_back(*jt);
+                jt = S.pending.erase(jt);
+                n_u = n2;
+                m_u = m2;
+            }
             return batch;
         }
     }
@@ -199,6 +358,10 @@ static std::vector<Request> take_batch(Server &S, Slot &sl, size_t budget, bool 
 }
 
 // A large request on the slot's fused-kernel workspace (grown if needed).
+// The lane's requests: one alone is solved in place; several are solved as
+// one union graph (see k_lane_gather / k_lane_scatter).
+static cudaError_t launch_lane(Server &S, Slot &sl, const std::vector<Request> &reqs, bool alone);
+
 static cudaError_t launch_big(Server &S, Slot &sl, const Request &r, bool alone)
 {
     const uint32_t n = (uint32_t)r.n, m = (uint32_t)r.m;
@@ -239,6 +402,100 @@ static cudaError_t launch_big(Server &S, Slot &sl, const Request &r, bool alone)
     if (e == cudaSuccess)
         e = cudaEventRecord(sl.done, sl.stream);
     sl.tickets.assign(1, r.ticket);
+    return e;
+}
+
+static cudaError_t launch_lane(Server &S, Slot &sl, const std::vector<Request> &reqs, bool alone)
+{
+    if (reqs.size() == 1)
+        return launch_big(S, sl, reqs[0], alone);
+    const int k = (int)reqs.size();
+    uint64_t n_u = 0, m_u = 0;
+    for (const Request &r : reqs) {
+        n_u += (uint64_t)r.n;
+        m_u += (uint64_t)r.m;
+    }
+    // the union's buffer (an outgrown one is kept until the server stops, as
+    // the lane workspaces are: freeing it now would wait for every stream)
+    const size_t need = union_bytes(n_u, m_u);
+    if (!S.ubuf || need > S.ubuf_bytes) {
+        std::lock_guard<std::mutex> lk(S.mu);
+        const size_t grow = std::max(need, 2 * S.ubuf_bytes);
+        if (S.ubuf)
+            S.retired.emplace_back(S.ubuf, S.ubuf_bytes);
+        S.ubuf = nullptr;
+        S.ubuf_bytes = 0;
+        cudaError_t e = cudaMalloc(&S.ubuf, grow);
+        if (e != cudaSuccess) {
+            S.ubuf = nullptr;
+            return e;
+        }
+        S.ubuf_bytes = grow;
+        S.in_use += grow;
+    }
+    if (!sl.h_lane) {
+        cudaError_t e = cudaMallocHost((void **)&sl.h_lane, sizeof(LaneDesc) * kLaneBatch);
+        if (e != cudaSuccess) {
+            sl.h_lane = nullptr;
+            return e;
+        }
+    }
+    char *p = (char *)S.ubuf;
+    LaneDesc *d_desc = (LaneDesc *)p;
+    p += al256(sizeof(LaneDesc) * kLaneBatch);
+    uint32_t *flags = (uint32_t *)p;
+    p += al256(4 * kLaneBatch);
+    int32_t *stat = (int32_t *)p;
+    p += al256(4 * kLaneBatch);
+    int64_t *ucnt = (int64_t *)p;
+    p += al256(8);
+    int32_t *us = (int32_t *)p;
+    p += al256(4 * m_u);
+    int32_t *ud = (int32_t *)p;
+    p += al256(4 * m_u);
+    uint32_t *uw = (uint32_t *)p;
+    p += al256(4 * m_u);
+    int32_t *uo = (int32_t *)p;
+    uint32_t vb = 0, eb = 0, max_m = 1;
+    for (int i = 0; i < k; i++) {
+        const Request &r = reqs[i];
+        sl.h_lane[i] = LaneDesc{r.src, r.dst, (const uint32_t *)r.w, r.out, r.out_count,
+                                (uint32_t)r.n, (uint32_t)r.m, vb, eb};
+        vb += (uint32_t)r.n;
+        eb += (uint32_t)r.m;
+        max_m = std::max<uint32_t>(max_m, (uint32_t)r.m);
+    }
+    cudaError_t e = cudaMemcpyAsync(d_desc, sl.h_lane, sizeof(LaneDesc) * k,
+                                    cudaMemcpyHostToDevice, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(flags, 0, 4 * kLaneBatch, sl.stream);
+    if (e != cudaSuccess)
+        return e;
+    const uint32_t gx = std::min<uint32_t>((max_m + 1023) / 1024, 256);
+    k_lane_gather<<<dim3(gx, k), 256, 0, sl.stream>>>(d_desc, reqs[0].wt, us, ud, uw, flags);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    // the union, solved by the fused kernel in the lane workspace
+    Request u = reqs[0];
+    u.n = (int32_t)n_u;
+    u.m = (int64_t)m_u;
+    u.src = us;
+    u.dst = ud;
+    u.w = uw;
+    u.out = uo;
+    u.out_count = ucnt;
+    e = launch_big(S, sl, u, alone);
+    if (e != cudaSuccess)
+        return e;
+    k_lane_scatter<<<k, 256, 0, sl.stream>>>(d_desc, uo, ucnt, flags, stat);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaEventRecord(sl.done, sl.stream);  // after the cut-out
+    sl.tickets.clear();
+    for (const Request &r : reqs)
+        sl.tickets.push_back(r.ticket);
+    sl.lane_k = k;
     return e;
 }
 
@@ -336,7 +593,7 @@ static void server_loop(Server *Sp)
         free_slot->big = big;
         lk.unlock();
         cudaError_t e =
-            big ? launch_big(S, *free_slot, batch[0], alone) : launch_batch(S, *free_slot, batch);
+            big ? launch_lane(S, *free_slot, batch, alone) : launch_batch(S, *free_slot, batch);
         if (e != cudaSuccess) {
             cudaGetLastError();
             std::lock_guard<std::mutex> g(S.mu);
@@ -353,6 +610,7 @@ static void server_loop(Server *Sp)
             S.inflight--;
             free_slot->busy = false;
             free_slot->big = false;
+            free_slot->lane_k = 0;
             free_slot->tickets.clear();
             if (free_slot->ws) {
                 cudaFreeAsync(free_slot->ws, free_slot->stream);
@@ -456,8 +714,12 @@ mst_status server_stop(mst_handle h)
             cudaFreeHost(sl.h_desc);
         if (sl.d_desc)
             cudaFree(sl.d_desc);
+        if (sl.h_lane)
+            cudaFreeHost(sl.h_lane);
     }
     single_release(S->lane);
+    if (S->ubuf)
+        cudaFree(S->ubuf);
     for (auto &r : S->retired)
         cudaFree(r.first);
     const mst_status st = S->error == cudaSuccess ? MST_OK : MST_ERR_CUDA;

@@ -184,3 +184,56 @@ def test_serving_bad_request_does_not_poison_its_batch(lib_built):
     finally:
         B.mst_server_stop(h)
         B.mst_destroy(h)
+
+
+def test_serving_lane_unions(lib_built):
+    """Requests for the fused lane that queue up behind one another are solved
+    together as one union graph: each must still get the oracle's tree and
+    its own status (a NaN weight and an out-of-range vertex id in two of
+    them, a forest in a third), with uint32 and float32 requests in separate
+    unions."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    graphs = []
+    for i in range(14):
+        wts = "f32" if i % 3 else "u32"
+        graphs.append(gg.random_connected(20000 + 3000 * i, 60000 + 9000 * i, 500 + i,
+                                          weights=wts))
+    nan = graphs[4]  # f32
+    nan.w = nan.w.copy()
+    nan.w[11] = np.float32("nan")
+    badv = graphs[7]
+    badv.dst = badv.dst.copy()
+    badv.dst[5] = badv.n + 9
+    a = gg.random_connected(30000, 90000, 520, weights="f32")
+    b = gg.random_connected(12000, 36000, 521, weights="f32")
+    forest = gg.Graph(a.n + b.n + 7, np.r_[a.src, b.src + a.n].astype(np.int32),
+                      np.r_[a.dst, b.dst + a.n].astype(np.int32), np.r_[a.w, b.w], "forest")
+    graphs.insert(9, forest)
+    h = B.mst_create(0, 0)
+    try:
+        assert B.mst_server_start(h, 1, 64) == B.MST_OK
+        reqs = submit_all(h, graphs)
+        res = wait_all(h, reqs)
+        assert B.mst_server_drain(h) == B.MST_OK
+        for t, g, out, cnt, _ in reqs:
+            st, _ = res[t]
+            got = out[: int(cnt.item())].cpu().numpy().astype(np.int64)
+            if g is nan or g is badv:
+                assert st == B.MST_ERR_INVALID_ARG, B.mst_status_string(st)
+                # the same tree as the graph alone (a bad edge ignored, a NaN
+                # weight sorting last), which the oracle does not define
+                s2, d2, w2 = to_dev(g.src, g.dst, g.w)
+                ids, st2 = B.solve(h, g.n, s2, d2, w2, check=False)
+                assert st2 == B.MST_ERR_INVALID_ARG
+                assert np.array_equal(got, ids.cpu().numpy().astype(np.int64))
+                continue
+            if g is forest:
+                assert st == B.MST_ERR_DISCONNECTED, B.mst_status_string(st)
+                assert int(cnt.item()) == g.n - oracle.components(g.n, g.src, g.dst)
+            else:
+                assert st == B.MST_OK, (g.name, B.mst_status_string(st))
+            assert np.array_equal(got, oracle.kruskal(g.n, g.src, g.dst, g.w)), g.name
+    finally:
+        B.mst_server_stop(h)
+        B.mst_destroy(h)

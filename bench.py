@@ -624,10 +624,18 @@ def batched_measure(B, h, stream, b, steps, warmup, per_graph_sample, sample_ora
     return block
 
 
+def _gen_workers() -> int:
+    """Worker processes for making a batch of graphs (spawned, so safe after
+    the first CUDA call)."""
+    return max(1, min(16, os.cpu_count() or 1))
+
+
 def batched_block(B, h, stream, args, per_graph_sample=64):
     """The C4 batch (4,096 graphs) measured for the headline line."""
     from paper_2005_06913_gb300 import graphgen as gg
-    b = gg.batched(args.graphs, 64, 65536, 8, gg.SEED_BASE + 3)
+    # the graphs are made by spawned worker processes (the same batch as one
+    # process makes: each graph depends only on its sub-seed)
+    b = gg.batched(args.graphs, 64, 65536, 8, gg.SEED_BASE + 3, workers=_gen_workers())
     blk = batched_measure(B, h, stream, b, args.steps, args.warmup, per_graph_sample,
                           sample_oracle=32)
     for k in ("total_ms", "window", "latency"):
@@ -663,7 +671,7 @@ def run_batched(args):
         build_mod.build()
     if dist is not None:
         dist.barrier()
-    full = gg.batched(args.graphs, 64, 65536, 8, gg.SEED_BASE + 3)
+    full = gg.batched(args.graphs, 64, 65536, 8, gg.SEED_BASE + 3, workers=_gen_workers())
     mine = shard_graphs(np.diff(full.edge_off), ws, rank) if ws > 1 else np.arange(full.G)
     b = sub_batch(full, mine) if ws > 1 else full
     stream = torch.cuda.current_stream()
@@ -725,7 +733,7 @@ def run_serving(args):
 
     # the pool is made before the first CUDA call (its worker processes are
     # spawned, never forked from a process that holds a GPU context)
-    workers = max(1, min(16, (os.cpu_count() or 1)))
+    workers = _gen_workers()
     t_gen = time.perf_counter()
     pool = gg.serving_pool(args.pool, 1024, args.serve_nmax, 6, gg.SEED_BASE + 4, workers=workers)
     t_gen = time.perf_counter() - t_gen

@@ -83,6 +83,7 @@ struct Ctl {
     uint32_t tail_cnt[kMaxRounds + 2];  // tail edge-list lengths (fused schedule)
     uint32_t tail_nn[kMaxRounds + 2];   // components after each tail round
     uint32_t tail_added;                // tree edges the tail added
+    uint32_t tail_rounds;               // rounds the tail ran
     uint32_t tick_find0;                // tile tickets of the fused kernel's balanced phases
     uint32_t tick_hook[kMaxRounds + 2];
     uint32_t tick_comp[kMaxRounds + 2];
@@ -109,6 +110,7 @@ struct Ws {
     uint2 *eends;              // current endpoints of a possible minimum edge, by input id
     unsigned long long *desc;  // look-back descriptors (emit of the graph schedule)
     uint32_t *emit_cnt;        // tree edges per emit chunk (fused schedule)
+    uint32_t *emit_cta;        // tree edges in each CTA's range of emit chunks
     uint32_t *bar;             // grid-barrier counters of the fused kernel
     unsigned long long *pair_tab;  // lightest key per component pair (tail)
     uint4 *tl[2];                  // tail edge lists (a, b, weight_bits, input id)

@@ -117,7 +117,6 @@ struct Ws {
     unsigned long long *tmin;      // tail: minimum key per component
     int32_t *tpar;                 // tail: hook pointers, then roots
     int32_t *tnid;                 // tail: new ids of the roots
-    uint32_t *ttouch;              // tail: pair slots written in a round
     uint32_t n_cap, m_cap, desc_cap;
 };
 

@@ -967,11 +967,13 @@ __device__ __forceinline__ void log_phase(Ctl *c, uint8_t kind, uint32_t round =
 //     list needs no order: the key names the edge);
 //   roots: every component finds its root; roots take dense new ids;
 //   merge: each edge between two different new components offers its key to
-//     the slot of that pair, and the first writer of a slot records it;
-//   next list: the recorded slots, read and reset, are the next round's list
-//     and offer their keys to their components (the next find-min).
-// So parallel edges are merged every round and a round costs O(list), not
-// O(table).  The rounds run on a team of CTAs sized to the list (one CTA per
+//     the slot of that pair (fire-and-forget);
+//   next list: the non-empty slots of the new components' table, read and
+//     reset, are the next round's list and offer their keys to their
+//     components (the next find-min).
+// So parallel edges are merged every round, and a round costs O(list) plus
+// a scan of the (shrinking) table of the new components' pairs.  The rounds
+// run on a team of CTAs sized to the list (one CTA per
 // kTailEdgesPerThread edges a thread, never growing): a team of one keeps
 // the per-component arrays in shared memory once at most kTailLocalN
 // components are left, and syncs with block barriers,
@@ -1191,51 +1193,57 @@ __device__ void tail_rounds(const Ws &ws, Ctl *c, uint32_t n_r, uint32_t m_r, ui
         if (aborted)
             return;
         const uint32_t n_next = ld_volatile_u32(nn);
-        // merge: relabel, offer to the pair slot; first writers record slots
-        uint32_t *touched = &c->tail_cnt[tr + 1];
-        const size_t steps = (m_r + nthr - 1) / nthr;  // every lane runs the same trip count
-        for (size_t k = 0; k < steps; k++) {
-            const size_t e = tid + k * nthr;
-            bool first = false;
-            uint32_t slot = 0;
-            if (e < m_r) {
-                const uint4 r = __ldcg(L + e);
-                const uint32_t A = (uint32_t)tnid[tpar[r.x]], B = (uint32_t)tnid[tpar[r.y]];
-                if (A != B) {
-                    slot = (A < B ? A : B) * n_next + (A < B ? B : A);
-                    const unsigned long long key = make_key(r.z, r.w);
-                    if (key < __ldcg(ws.pair_tab + slot))
-                        first = atomicMin(ws.pair_tab + slot, key) == kNoEdge;
-                }
-            }
-            warp_append_u32(ws.ttouch, touched, first, slot);
+        // merge: relabel, offer each key to its pair's slot (fire-and-forget:
+        // no thread waits on the table here)
+        for (size_t e = tid; e < m_r; e += nthr) {
+            const uint4 r = __ldcg(L + e);
+            const uint32_t A = (uint32_t)tnid[tpar[r.x]], B = (uint32_t)tnid[tpar[r.y]];
+            if (A != B)
+                red_min_u64(ws.pair_tab + (A < B ? A : B) * n_next + (A < B ? B : A),
+                            make_key(r.z, r.w));
         }
         for (size_t v = tid; v < n_next; v += nthr)
             tmin[v] = kNoEdge;
         sync();
         if (aborted)
             return;
-        // next list: the recorded slots, reset; find-min of the next round
-        const uint32_t m_next = ld_volatile_u32(touched);
-        for (size_t i = tid; i < m_next; i += nthr) {
-            const uint32_t slot = __ldcg(ws.ttouch + i);
-            const unsigned long long key = __ldcg(ws.pair_tab + slot);
-            ws.pair_tab[slot] = kNoEdge;
-            const uint32_t a = slot / n_next, b = slot % n_next;
-            Ln[i] = make_uint4(a, b, (uint32_t)(key >> 32), (uint32_t)key);
-            if (local) {
-                atomicMin((unsigned long long *)&tmin[a], key);
-                atomicMin((unsigned long long *)&tmin[b], key);
-            } else {
-                offer_min(ws.tmin + a, key);
-                offer_min(ws.tmin + b, key);
+        // next list: the non-empty slots of the n_next x n_next table, reset;
+        // find-min of the next round.  (A scan of the table replaced recording
+        // first writers, which cost each merge offer a returning atomic: on
+        // the 4,096 / 32,768 random graph the first tail round took 20 us.)
+        uint32_t *touched = &c->tail_cnt[tr + 1];
+        const size_t slots = (size_t)n_next * n_next;
+        const size_t steps = (slots + nthr - 1) / nthr;  // every lane runs the same trip count
+        for (size_t k = 0; k < steps; k++) {
+            const size_t i = tid + k * nthr;
+            bool keep = false;
+            uint4 rec = make_uint4(0, 0, 0, 0);
+            if (i < slots) {
+                const uint32_t a = (uint32_t)(i / n_next), b = (uint32_t)(i % n_next);
+                if (a < b) {
+                    const unsigned long long key = __ldcg(ws.pair_tab + i);
+                    if (key != kNoEdge) {
+                        keep = true;
+                        ws.pair_tab[i] = kNoEdge;
+                        rec = make_uint4(a, b, (uint32_t)(key >> 32), (uint32_t)key);
+                        if (local) {
+                            atomicMin((unsigned long long *)&tmin[a], key);
+                            atomicMin((unsigned long long *)&tmin[b], key);
+                        } else {
+                            offer_min(ws.tmin + a, key);
+                            offer_min(ws.tmin + b, key);
+                        }
+                    }
+                }
             }
+            warp_append(Ln, touched, keep, rec);
         }
         for (size_t v = tid; v < n_next; v += nthr)
             tpar[v] = (int32_t)v;
         sync();
         if (aborted)
             return;
+        const uint32_t m_next = ld_volatile_u32(touched);
         if (bid == 0 && threadIdx.x == 0 && r_base + tr + 1 <= (uint32_t)kMaxRounds) {
             c->stat_m[r_base + tr + 1] = m_next;
             c->stat_n[r_base + tr + 1] = n_next;
@@ -1683,7 +1691,6 @@ size_t single_bytes(uint32_t n_cap, uint32_t m_cap)
     b += align_up(tn * tn * 8);                  // pair table
     b += 2 * align_up(tp * 16);                  // tail lists
     b += align_up((size_t)kTailMaxN * 8) + 2 * align_up((size_t)kTailMaxN * 4);
-    b += align_up(tp * 4);                       // touched slots
     return b;
 }
 
@@ -1853,7 +1860,6 @@ cudaError_t single_reserve(Single &s, int device, uint32_t n, uint32_t m)
     s.ws.tmin = (unsigned long long *)take((size_t)kTailMaxN * 8);
     s.ws.tpar = (int32_t *)take((size_t)kTailMaxN * 4);
     s.ws.tnid = (int32_t *)take((size_t)kTailMaxN * 4);
-    s.ws.ttouch = (uint32_t *)take(tp * 4);
     s.ws.n_cap = n_cap;
     s.ws.m_cap = m_cap;
     MST_TRY(cudaMemset(s.ws.ctl, 0, sizeof(Ctl)));

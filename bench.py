@@ -753,6 +753,23 @@ def run_serving(args):
     po, pc = outs.data_ptr(), cnts.data_ptr()
     rng = np.random.default_rng(5)
     budget = 120 << 30
+    # untimed warm-up: every pool graph once through a server, so that each
+    # kernel's first launch (module loading) and the stream-ordered pools'
+    # growth happen before any timed stream
+    h = B.mst_create(0, budget)
+    B.mst_server_start(h, args.streams, args.max_batch)
+    for g0 in range(0, pool.G, ring):
+        waiting = []
+        for j, g in enumerate(range(g0, min(pool.G, g0 + ring))):
+            e0 = int(g_e0[g])
+            st, t = B.mst_submit(h, B.MST_W_F32, int(g_n[g]), int(g_m[g]), ps + 4 * e0,
+                                 pd + 4 * e0, pw + 4 * e0, po + 4 * nmax * j, pc + 8 * j)
+            waiting.append(t)
+        while waiting:
+            waiting = [t for t in waiting if not B.mst_poll(h, t)[1]]
+            time.sleep(0.0005)
+    B.mst_server_stop(h)
+    B.mst_destroy(h)
     results = []
     streams_of_rate = {}
     for rate in [float(x) for x in args.rates.split(",")]:
@@ -816,6 +833,10 @@ def run_serving(args):
     # requests still queued then count with their waiting time so far (a
     # lower bound, which favours this arm).
     h = B.mst_create(0, 0)
+    big = int(np.argmax(g_m))  # untimed: sizes the workspace for the largest graph
+    B.mst_solve_ex(h, B.MST_W_F32, int(g_n[big]), int(g_m[big]), ps + 4 * int(g_e0[big]),
+                   pd + 4 * int(g_e0[big]), pw + 4 * int(g_e0[big]), po, pc)
+    torch.cuda.current_stream().synchronize()
     sequential = []
     for rate, (arrivals, picks) in streams_of_rate.items():
         lat = []

@@ -63,15 +63,19 @@ def _code_only(text: str) -> str:
     return "\n".join(l.rstrip() for l in text.splitlines() if l.strip())
 
 
-def kernel_source_sha(src_dir=None) -> str:
+def kernel_source_sha(src_dir=None, files=("mst_common.cuh", "mst_single.cu")) -> str:
     """sha256 prefix of the code (comments stripped) of the sources that
-    define the fused single-graph kernel: its tile bodies and device helpers."""
+    define a kernel: by default the fused single-graph kernel's tile bodies
+    and device helpers (the batched kernel: mst_common.cuh + mst_batched.cu)."""
     import hashlib
     src = src_dir or os.path.join(ROOT, "paper_2005_06913_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("mst_common.cuh", "mst_single.cu"):
+    for f in files:
         h.update(_code_only(open(os.path.join(src, f)).read()).encode())
     return h.hexdigest()[:16]
+
+
+BATCHED_FILES = ("mst_common.cuh", "mst_batched.cu")
 
 
 TRAFFIC_WORKLOAD = {1: None, 2: "grid2d_1024x1024", 3: "rmat_scale22"}
@@ -91,6 +95,26 @@ def traffic_for(kernel: str, workload):
                 and f[3] == workload):
             return float(f[2])
     return None
+
+
+def batched_traffic_for(total_edges: int):
+    """DRAM bytes of one batched launch over `total_edges` edges, scaled by
+    edges from the committed capture of a smaller batch of the same graph
+    distribution (profiles/ncu_traffic.txt: "k_b_solve sha bytes
+    edges=E ..."), or (None, None) when absent or taken on other code."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(p) or total_edges <= 0:
+        return None, None
+    sha = kernel_source_sha(files=BATCHED_FILES)
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == "k_b_solve" and f[1] == sha \
+                and f[3].startswith("edges="):
+            e_cap = int(f[3].split("=", 1)[1])
+            return float(f[2]) * total_edges / e_cap, (
+                f"ncu capture of a {e_cap:,}-edge batch of the same graph distribution "
+                f"({float(f[2]) / 1e9:.3f} GB), scaled by edges")
+    return None, None
 
 
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (context beside the measured peak)
@@ -565,6 +589,7 @@ def batched_measure(B, h, stream, b, steps, warmup, per_graph_sample, sample_ora
     # the tree ids, the counts and the offset tables
     lb_bytes = 12.0 * tm + 4.0 * max(tn - b.G, 0) + 8.0 * b.G + 16.0 * (b.G + 1)
     mean_s = statistics.mean(lat) * 1e-3
+    traffic, traffic_src = batched_traffic_for(tm)
     block = {"total_ms": sum(lat), "window": (t0, t1), "latency": lat,
              "value": b.G / mean_s, "unit": "graphs/s", "steps": steps,
              "ms_per_step": statistics.mean(lat), "ms_per_step_median": statistics.median(lat),
@@ -579,7 +604,9 @@ def batched_measure(B, h, stream, b, steps, warmup, per_graph_sample, sample_ora
                           "alg_bytes_model": "lower bound: input read once (12 B/edge), tree ids "
                                              "(4 B), counts (8 B/graph) and offsets",
                           "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",
-                          "traffic": None},
+                          "traffic": traffic, "traffic_source": traffic_src,
+                          "traffic_GBps": traffic / mean_s / 1e9 if traffic else None,
+                          "traffic_frac": traffic / mean_s / 1e9 / hbm_peak if traffic else None},
              "oracle_checked_graphs": checked,
              "gpu_launches": 3 * steps,
              "device_status": B.mst_status_string(status)}

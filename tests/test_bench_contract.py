@@ -45,6 +45,24 @@ def test_traffic_table_lookup(tmp_path, monkeypatch):
     assert bench.traffic_for("k_other", "grid2d_1024x1024") is None
 
 
+def test_batched_traffic_scales_by_edges(tmp_path, monkeypatch):
+    sha_b = bench.kernel_source_sha(files=bench.BATCHED_FILES)
+    assert len(sha_b) == 16 and sha_b != bench.kernel_source_sha()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.txt").write_text(
+        f"k_solve {sha_b} 5 grid2d_1024x1024\n"
+        f"k_b_solve 0000000000000000 7 edges=10 other_code\n"
+        f"k_b_solve {sha_b} 1000 edges=250 batched_small\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda files=None: sha_b)
+    traffic, src = bench.batched_traffic_for(1000)
+    assert traffic == 4000.0 and "250-edge batch" in src  # 1000 B for 250 edges, x4
+    assert bench.batched_traffic_for(0) == (None, None)
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda files=None: "f" * 16)
+    assert bench.batched_traffic_for(1000) == (None, None)  # captured on other code
+
+
 @pytest.mark.parametrize("xs,p50,p99", [([], None, None), ([5.0], 5.0, 5.0),
                                         (list(range(1, 101)), 51, 99)])
 def test_percentiles(xs, p50, p99):

@@ -299,15 +299,16 @@ __host__ __device__ __forceinline__ size_t vert_bytes(uint32_t n)
     return 2 * al16((size_t)n * 8) + 3 * al16((size_t)n * 4);
 }
 
-// Lays the per-vertex arrays for up to n vertices out at the start of `sm`
-// and gives the merging tail's pair table the shared memory left after them
-// (tail_n = 0 when too little is left).
+// Lays the per-vertex arrays for up to n vertices out at the start of `sm`,
+// the second minimum array last, and gives the merging tail's pair table the
+// shared memory from that array on (tail_n = 0 when too little is left).
+// The second minimum array is dead whenever the pair table is in use: the
+// tail starts after a round's hook, that round's compaction (the only writer
+// of the next minima) does not run, and the tail's own minima are in mA.
 __device__ __forceinline__ void carve_vertex(GraphArrays &A, char *sm, size_t budget, uint32_t n)
 {
     char *p = sm;
     A.mA = (unsigned long long *)p;
-    p += al16((size_t)n * 8);
-    A.mB = (unsigned long long *)p;
     p += al16((size_t)n * 8);
     A.parent = (int32_t *)p;
     p += al16((size_t)n * 4);
@@ -315,6 +316,7 @@ __device__ __forceinline__ void carve_vertex(GraphArrays &A, char *sm, size_t bu
     p += al16((size_t)n * 4);
     A.lab = (int32_t *)p;
     p += al16((size_t)n * 4);
+    A.mB = (unsigned long long *)p;
     const size_t left = budget - (size_t)(p - sm);
     uint32_t tn = kBTailMaxN;
     while (tn >= 8 && (size_t)tri_size(tn) * 8 > left)

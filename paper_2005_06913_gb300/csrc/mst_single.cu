@@ -879,7 +879,7 @@ constexpr uint32_t kBarSpinLimit = 1u << 22;
 // Barrier among CTAs [0, nb) (all co-resident).  Returns true in every
 // thread of the CTA when the solve has timed out (this CTA's wait ran out,
 // or another CTA's did before): the data of the phase just ended may then
-// be incomplete, so the caller must not start the next phase.  The verdict
+// be incomplete, so the caller must not start the next phase.  The outcome
 // is read once by thread 0 and broadcast, so a CTA never splits on it.
 __device__ __forceinline__ bool team_sync(uint32_t *counter, uint32_t nb, uint32_t *status,
                                           uint32_t spin_limit)

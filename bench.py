@@ -516,6 +516,10 @@ def run_ours(args):
         line["batched"] = batched_block(B, h, stream, args, per_graph_sample=64)
         launches += line["batched"]["gpu_launches"]
         line["gpu_launches_all_blocks"] = launches
+        try:
+            line["serving"] = serving_block(B)
+        except Exception as e:  # noqa: BLE001 (the headline line prints either way)
+            line["serving"] = {"error": f"{type(e).__name__}: {e}"}
     B.mst_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -674,6 +678,26 @@ def batched_block(B, h, stream, args, per_graph_sample=64):
     return blk
 
 
+def serving_block(B):
+    """C5 in short for the headline line: the pool, server and comparison of
+    `--workload serving` (1,024 random connected graphs, n log-uniform in
+    [1,024, 2^20], degree 6), at 10,000 and 20,000 requests/s for 5 s each.
+    The full sweep (1k-50k/s, 60 s per rate) is that workload."""
+    from paper_2005_06913_gb300 import graphgen as gg
+    t = time.perf_counter()
+    pool = gg.serving_pool(1024, 1024, 1 << 20, 6, gg.SEED_BASE + 4, workers=_gen_workers())
+    t_gen = time.perf_counter() - t
+    blk = serving_measure(B, pool, [10000.0, 20000.0], 5.0, 4, 256)
+    blk["workload"] = ("C5 serving, short: pool of 1,024 random connected graphs (replayed), "
+                       "n log-uniform [1024, 1048576], degree 6, float32 weights; open-loop "
+                       "Poisson arrivals at 10,000 and 20,000 requests/s for 5 s each "
+                       "(the full sweep is --workload serving)")
+    blk["pool_edges"] = int(pool.edge_off[-1])
+    blk["pool_gen_s"] = round(t_gen, 1)
+    blk["streams"], blk["max_batch"] = 4, 256
+    return blk
+
+
 def run_batched(args):
     """C4: G independent random connected graphs (n log-uniform in
     [64, 65536], average degree 8) solved by one mst_solve_batched launch
@@ -766,6 +790,33 @@ def run_serving(args):
     t_gen = time.perf_counter() - t_gen
     torch.cuda.set_device(0)
     build_mod.build()
+    blk = serving_measure(B, pool, [float(x) for x in args.rates.split(",")], args.seconds,
+                          args.streams, args.max_batch)
+    best = max(blk["sweep"], key=lambda r: r["graphs_per_s"])
+    line = {"metric": "served graphs/s at p50/p99 latency", "impl": "ours",
+            "value": best["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"C5 serving: pool of {pool.G} random connected graphs "
+                                   f"(replayed), n log-uniform [1024, {args.serve_nmax}], degree 6, "
+                                   f"float32 weights; open-loop Poisson arrivals for "
+                                   f"{args.seconds} s per rate",
+                       "pool_edges": int(pool.edge_off[-1]), "pool_gen_s": round(t_gen, 1),
+                       "streams": args.streams, "max_batch": args.max_batch,
+                       "memory_budget_bytes": blk["memory_budget_bytes"]}}
+    line.update({k: blk[k] for k in ("sweep", "same_streams_one_solve_at_a_time", "side_by_side",
+                                     "knee_graphs_per_s")})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serving_measure(B, pool, rates, seconds, streams, max_batch):
+    """Serves `pool` (a Batch of float32 graphs) as open-loop Poisson streams
+    at each rate for `seconds` through the continuous-batching server, then
+    the same arrival streams one solve at a time.  Returns the sweep, the
+    one-at-a-time rows, both side by side, the saturation knees and the
+    memory budget."""
+    import torch
     dev = lambda a: torch.from_numpy(a.view(np.int32) if a.dtype != np.int64 else a).cuda()
     s, d, w = dev(pool.src), dev(pool.dst), dev(pool.w)
     # raw device addresses of each pool graph (no tensor views in the arrival loop)
@@ -784,7 +835,7 @@ def run_serving(args):
     # kernel's first launch (module loading) and the stream-ordered pools'
     # growth happen before any timed stream
     h = B.mst_create(0, budget)
-    B.mst_server_start(h, args.streams, args.max_batch)
+    B.mst_server_start(h, streams, max_batch)
     for g0 in range(0, pool.G, ring):
         waiting = []
         for j, g in enumerate(range(g0, min(pool.G, g0 + ring))):
@@ -792,18 +843,21 @@ def run_serving(args):
             st, t = B.mst_submit(h, B.MST_W_F32, int(g_n[g]), int(g_m[g]), ps + 4 * e0,
                                  pd + 4 * e0, pw + 4 * e0, po + 4 * nmax * j, pc + 8 * j)
             waiting.append(t)
+        t_wait = time.perf_counter()
         while waiting:
             waiting = [t for t in waiting if not B.mst_poll(h, t)[1]]
+            if time.perf_counter() - t_wait > 300.0:
+                raise RuntimeError(f"serving warm-up: {len(waiting)} requests not done in 300 s")
             time.sleep(0.0005)
     B.mst_server_stop(h)
     B.mst_destroy(h)
     results = []
     streams_of_rate = {}
-    for rate in [float(x) for x in args.rates.split(",")]:
+    for rate in rates:
         h = B.mst_create(0, budget)
-        B.mst_server_start(h, args.streams, args.max_batch)
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * args.seconds) + 1))
-        arrivals = arrivals[arrivals < args.seconds]
+        B.mst_server_start(h, streams, max_batch)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds) + 1))
+        arrivals = arrivals[arrivals < seconds]
         picks = rng.integers(0, pool.G, arrivals.shape[0])
         streams_of_rate[rate] = (arrivals, picks)
         tickets, lat, done_t = {}, [], []
@@ -814,10 +868,13 @@ def run_serving(args):
         # an overloaded stream is cut off at 1.2x its span: arrivals not yet
         # submitted then are counted as unserved (with their wait so far as a
         # lower bound on their latency), and requests in flight are drained
-        cut = 1.2 * args.seconds
+        cut = 1.2 * seconds
         unserved = 0
         while k < arrivals.shape[0] or tickets:
             now = time.perf_counter() - t_start
+            if now > cut + 300.0:  # the backlog drains in seconds; never wait without end
+                raise RuntimeError(f"serving at {rate}/s: {len(tickets)} requests not done "
+                                   f"{now - cut:.0f} s after the cut")
             if now > cut and k < arrivals.shape[0]:
                 unserved = int(arrivals.shape[0] - k)
                 lat.extend((now - arrivals[k:]) * 1e3)
@@ -868,7 +925,7 @@ def run_serving(args):
     for rate, (arrivals, picks) in streams_of_rate.items():
         lat = []
         t_start = time.perf_counter()
-        cut = 1.2 * args.seconds
+        cut = 1.2 * seconds
         served = 0
         for k in range(arrivals.shape[0]):
             now = time.perf_counter() - t_start
@@ -902,24 +959,10 @@ def run_serving(args):
                      "one_at_a_time": {"graphs_per_s": b_["graphs_per_s"],
                                        "p99_ms": b_["latency_ms"]["p99"]}}
                     for a, b_ in zip(results, sequential)]
-    best = max(results, key=lambda r: r["graphs_per_s"])
-    line = {"metric": "served graphs/s at p50/p99 latency", "impl": "ours",
-            "value": best["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"C5 serving: pool of {pool.G} random connected graphs "
-                                   f"(replayed), n log-uniform [1024, {args.serve_nmax}], degree 6, "
-                                   f"float32 weights; open-loop Poisson arrivals for "
-                                   f"{args.seconds} s per rate",
-                       "pool_edges": int(pool.edge_off[-1]), "pool_gen_s": round(t_gen, 1),
-                       "streams": args.streams, "max_batch": args.max_batch,
-                       "memory_budget_bytes": budget},
-            "sweep": results,
-            "same_streams_one_solve_at_a_time": sequential,
+    return {"sweep": results, "same_streams_one_solve_at_a_time": sequential,
             "side_by_side": side_by_side,
-            "knee_graphs_per_s": {"server": knee(results), "one_at_a_time": knee(sequential)}}
-    print(json.dumps(line), flush=True)
-    return 0
+            "knee_graphs_per_s": {"server": knee(results), "one_at_a_time": knee(sequential)},
+            "memory_budget_bytes": budget}
 
 
 PAPER_TABLE1 = ["Graph10K_3", "Graph10K_6", "Graph10K_9", "Graph100K_3", "Graph100K_6",

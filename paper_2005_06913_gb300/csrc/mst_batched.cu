@@ -898,7 +898,8 @@ __device__ void solve_graph(const Team &tm, uint32_t n, uint32_t m, const int32_
         tm.sync();
         m_r = run;
         n_r = n_next;
-        if (mig) {  // once per graph; carve_vertex only sets pointers (the new minima were cleared above)
+        if (mig) {  // once per graph; carve_vertex only sets pointers (the minima
+                    // were cleared above)
             carve_vertex(A, A.mig_sm, A.mig_budget, n_r);
             A.mig_sm = nullptr;
             mc = A.mA;
